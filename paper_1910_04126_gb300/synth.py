@@ -126,22 +126,23 @@ def stroke_images(n: int, seed: int, side: int = 28, samples: int = 200, sigma: 
     keep = rng.integers(s_lo, s_hi + 1, size=n)
     t = np.linspace(0.0, 1.0, samples)
     bern = np.stack([(1 - t) ** 3, 3 * t * (1 - t) ** 2, 3 * t ** 2 * (1 - t), t ** 3], axis=1)  # [S, 4]
-    coords = np.arange(1, side + 1, dtype=np.float64)
+    import torch  # CPU tensor ops only: fast multi-threaded rendering of the strokes
+
+    coords = torch.arange(1, side + 1, dtype=torch.float32)
+    inv = -1.0 / (2 * sigma * sigma)
     words, weights = [], []
     for lo in range(0, n, chunk):
         hi = min(n, lo + chunk)
-        c = np.einsum("sk,nmkd->nmsd", bern, ctrl[lo:hi])            # [m, 3, S, 2]
-        mask = (np.arange(3)[None, :] < n_strokes[lo:hi, None])       # [m, 3]
-        gx = np.exp(-((coords[None, None, None, :] - c[..., 0:1]) ** 2) / (2 * sigma * sigma))
-        gy = np.exp(-((coords[None, None, None, :] - c[..., 1:2]) ** 2) / (2 * sigma * sigma))
-        gx = gx * mask[:, :, None, None]
+        c = torch.from_numpy(np.einsum("sk,nmkd->nmsd", bern, ctrl[lo:hi]).astype(np.float32))  # [m, 3, S, 2]
+        mask = torch.from_numpy((np.arange(3)[None, :] < n_strokes[lo:hi, None]).astype(np.float32))
+        gx = torch.exp((coords - c[..., 0:1]).square() * inv) * mask[:, :, None, None]
+        gy = torch.exp((coords - c[..., 1:2]).square() * inv)
         gx = gx.reshape(hi - lo, 3 * samples, side)
         gy = gy.reshape(hi - lo, 3 * samples, side)
-        img = np.einsum("nsi,nsj->nij", gx, gy).reshape(hi - lo, side * side)
+        img = torch.bmm(gx.transpose(1, 2), gy).reshape(hi - lo, side * side).numpy()
+        order = np.argsort(-img, axis=1, kind="stable")
         for r in range(hi - lo):
-            s = int(keep[lo + r])
-            idx = np.argsort(-img[r], kind="stable")[:s]
-            idx = np.sort(idx)
+            idx = np.sort(order[r, : int(keep[lo + r])])
             words.append(idx.astype(np.int32))
             weights.append(img[r, idx].astype(np.float32))
     return csr_from_lists(words, weights)

@@ -1,0 +1,198 @@
+"""GPU parity of the quadtree, the supports and the batched Flowtree against the oracle.
+
+Bit-exact: ranks, lcp, supports (points and integer masses), saved flows
+(as sets of (item_a, item_b, flow, depth)).  Costs: FP32 within 1e-5 relative
+of the FP64 oracle.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1910_04126_gb300 import api, synth
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-5
+
+
+def build_both(points, levels, shift):
+    tree = api.Tree(torch.as_tensor(points, device="cuda"), levels, shift)
+    otree = O.OracleTree(points, levels, shift)
+    return tree, otree
+
+
+def oracle_supports(otree, docs):
+    return otree.embed_docs(docs.row_ptr, docs.word, docs.weight)
+
+
+def cases():
+    out = {}
+    w = synth.tiny(n_points=1000, n_db=300, n_queries=7)
+    out["tiny2d"] = (w.points, w.levels, w.shift, w.db, w.queries)
+    img_db = synth.stroke_images(150, 1)
+    img_q = synth.stroke_images(5, 2)
+    out["grid"] = (synth.grid_points(), 12, synth.random_shift(2, 3), img_db, img_q)
+    rng = np.random.default_rng(4)
+    p1 = rng.random((500, 1)).astype(np.float32)
+    out["line"] = (p1, 14, synth.random_shift(1, 5), synth.uniform_docs(500, 80, 1, 40, 6),
+                   synth.uniform_docs(500, 3, 1, 40, 7))
+    v30 = synth.mixture_vocab(3000, 30, 50, 0.3, 8)
+    out["d30"] = (v30, 12, synth.random_shift(30, 9), synth.zipf_docs(3000, 120, 10, median=40, s_lo=5, s_hi=200),
+                  synth.zipf_docs(3000, 4, 11, median=40, s_lo=5, s_hi=200))
+    v300 = synth.mixture_vocab(4000, 300, 100, 0.3, 12)
+    out["d300"] = (v300, 12, synth.random_shift(300, 13),
+                   synth.zipf_docs(4000, 100, 14, median=80, s_lo=20, s_hi=400),
+                   synth.zipf_docs(4000, 3, 15, median=80, s_lo=20, s_hi=400))
+    return out
+
+
+CASES = cases()
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_tree_bit_exact(name):
+    pts, L, shift, _, _ = CASES[name]
+    tree, otree = build_both(pts, L, shift)
+    rop, por, lcp, sh = tree.export()
+    orop, opor = otree.ranks()
+    assert np.array_equal(rop.astype(np.int64), orop)
+    assert np.array_equal(por.astype(np.int64), opor)
+    assert np.array_equal(lcp.astype(np.int32), otree.lcp())
+    assert np.array_equal(sh, shift)
+    assert tree.info.phi_log2 == otree.phi_log2
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_supports_bit_exact(name):
+    pts, L, shift, db, _ = CASES[name]
+    tree, otree = build_both(pts, L, shift)
+    D = api.Docs.from_csr(tree, db)
+    ptr, pt, ms = D.export()
+    S = oracle_supports(otree, db)
+    assert np.array_equal(ptr, S.ptr)
+    assert np.array_equal(pt.astype(np.int64), S.point)
+    assert np.array_equal(ms.astype(np.int64), S.mass)
+
+
+def _oracle_costs(otree, pts, SA, SB, pa, pb):
+    return otree.flowtree_batch(pts, SA, SB, pa, pb, n_threads=4)
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_flowtree_cross_and_pairs_vs_oracle(name):
+    pts, L, shift, db, q = CASES[name]
+    tree, otree = build_both(pts, L, shift)
+    Dd, Dq = api.Docs.from_csr(tree, db), api.Docs.from_csr(tree, q)
+    Sd, Sq = oracle_supports(otree, db), oracle_supports(otree, q)
+    vocab = tree.points
+    # cross product queries x db
+    got = api.flowtree_batch(tree, vocab, Dq, Dd).cpu().numpy().astype(np.float64)
+    qa = np.repeat(np.arange(q.n), db.n)
+    qb = np.tile(np.arange(db.n), q.n)
+    ref = _oracle_costs(otree, pts, Sq, Sd, qa, qb)
+    np.testing.assert_allclose(got, ref, rtol=REL, atol=1e-30)
+    # explicit random pairs (db x db), including repeated and self pairs
+    rng = np.random.default_rng(0)
+    pa = rng.integers(0, db.n, 700)
+    pb = rng.integers(0, db.n, 700)
+    pb[:20] = pa[:20]
+    got2 = api.flowtree_batch(tree, vocab, Dd, Dd, pa, pb).cpu().numpy().astype(np.float64)
+    ref2 = _oracle_costs(otree, pts, Sd, Sd, pa, pb)
+    np.testing.assert_allclose(got2, ref2, rtol=REL, atol=1e-30)
+    assert np.all(got2[:20] == 0.0)
+    assert tree.status() == 0
+
+
+@pytest.mark.parametrize("name", ["tiny2d", "d300", "line"])
+def test_saved_flows_bit_exact(name):
+    pts, L, shift, db, _ = CASES[name]
+    tree, otree = build_both(pts, L, shift)
+    Dd = api.Docs.from_csr(tree, db)
+    Sd = oracle_supports(otree, db)
+    rng = np.random.default_rng(1)
+    pa = rng.integers(0, db.n, 200)
+    pb = rng.integers(0, db.n, 200)
+    flows = api.Flows(tree, Dd, Dd, pa, pb)
+    api.flowtree_batch(tree, tree.points, Dd, Dd, flows.pair_a, flows.pair_b, flows=flows)
+    got = flows.export()
+    for i in range(200):
+        ia, ib, f, dep = otree.flow(*Sd.doc(pa[i]), *Sd.doc(pb[i]))
+        ref = sorted(zip(ia.tolist(), ib.tolist(), f.tolist(), dep.tolist()))
+        g = got[i]
+        mine = sorted(zip(g[0].tolist(), g[1].tolist(), g[2].tolist(), g[3].tolist()))
+        assert mine == ref, i
+
+
+@pytest.mark.parametrize("name", ["tiny2d", "d300"])
+def test_plain_form_equals_batched(name):
+    pts, L, shift, db, q = CASES[name]
+    tree, _ = build_both(pts, L, shift)
+    Dd, Dq = api.Docs.from_csr(tree, db), api.Docs.from_csr(tree, q)
+    a = api.flowtree_batch(tree, tree.points, Dq, Dd)
+    b = api.flowtree_plain(tree, tree.points, Dq, Dd)
+    assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("cap", [32, 64, 96])
+def test_long_pairs_use_workspace_staging(cap):
+    # Pairs longer than the on-chip staging take the workspace path.
+    pts, L, shift, db, q = CASES["d300"]
+    tree, otree = build_both(pts, L, shift)
+    Dd, Dq = api.Docs.from_csr(tree, db), api.Docs.from_csr(tree, q)
+    ref = api.flowtree_batch(tree, tree.points, Dq, Dd).cpu().numpy()
+    tree.set_config(2, cap)
+    got = api.flowtree_batch(tree, tree.points, Dq, Dd).cpu().numpy()
+    assert np.array_equal(got, ref)
+    Sd, Sq = oracle_supports(otree, db), oracle_supports(otree, q)
+    qa = np.repeat(np.arange(q.n), db.n)
+    qb = np.tile(np.arange(db.n), q.n)
+    np.testing.assert_allclose(got, _oracle_costs(otree, pts, Sq, Sd, qa, qb), rtol=REL)
+
+
+def test_edge_cases_dirac_single_and_identical():
+    rng = np.random.default_rng(3)
+    pts = rng.random((257, 3)).astype(np.float32)
+    pts[5] = pts[6]  # duplicate coordinates, distinct points
+    shift = synth.random_shift(3, 4)
+    words = [np.array([5]), np.array([6]), np.array([0, 1, 2]), np.array([2, 1, 0]),
+             np.arange(0, 257), np.array([256]), np.array([3, 3, 3])]
+    weights = [np.ones(len(w), np.float32) for w in words]
+    weights[3] = np.array([3.0, 2.0, 1.0], np.float32)
+    docs = synth.csr_from_lists(words, weights)
+    tree, otree = build_both(pts, 10, shift)
+    D = api.Docs.from_csr(tree, docs)
+    S = oracle_supports(otree, docs)
+    n = docs.n
+    pa = np.repeat(np.arange(n), n)
+    pb = np.tile(np.arange(n), n)
+    got = api.flowtree_batch(tree, tree.points, D, D, pa, pb).cpu().numpy().astype(np.float64)
+    ref = otree.flowtree_batch(pts, S, S, pa, pb)
+    np.testing.assert_allclose(got, ref, rtol=REL, atol=1e-30)
+    assert got[0 * n + 1] == 0.0  # same coordinates, different points
+    for i in range(n):
+        assert got[i * n + i] == 0.0
+
+
+def test_rejects_bad_inputs():
+    pts = np.random.default_rng(0).random((10, 2)).astype(np.float32)
+    tree = api.Tree(torch.as_tensor(pts, device="cuda"), 6, synth.random_shift(2, 0))
+    bad = [synth.csr_from_lists([np.array([0, 1])], [np.array([1.0, -1.0], np.float32)]),
+           synth.csr_from_lists([np.array([0])], [np.array([0.0], np.float32)]),
+           synth.csr_from_lists([np.array([10])]),
+           synth.csr_from_lists([np.array([0])], [np.array([np.nan], np.float32)])]
+    for d in bad:
+        with pytest.raises(api._ffi.FlowtreeError):
+            api.Docs.from_csr(tree, d)
+    with pytest.raises(api._ffi.FlowtreeError):
+        api.Tree(torch.as_tensor(pts, device="cuda"), 0)
+    with pytest.raises(api._ffi.FlowtreeError):
+        api.Tree(torch.as_tensor(pts, device="cuda"), 6, np.array([2 ** 40 + 1, 0], np.uint64))
+    # a pair index out of range is caught by the kernel's bounds check and
+    # reported through the device status word; its cost is NaN
+    good = api.Docs.from_csr(tree, synth.csr_from_lists([np.array([1, 2])]))
+    out = api.flowtree_batch(tree, tree.points, good, good, np.array([0, 0]), np.array([3, 0]))
+    assert tree.status() == -1
+    o = out.cpu().numpy()
+    assert np.isnan(o[0]) and o[1] == 0.0
+    assert tree.status() == 0
