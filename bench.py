@@ -1,0 +1,466 @@
+"""Benchmark of the batched Flowtree on GB300.
+
+Workload (one "step"): the image-shaped configuration -- ground set = the
+28x28 integer grid, 60,000 database and 1,000 query distributions of 100-200
+pixels (synthetic Bezier strokes, mass proportional to intensity), quadtree
+with L = 12 -- Flowtree for every (query, database) pair (6e7 pairs) in one
+persistent launch, then the 10 nearest per query.  Inputs are resident in HBM;
+L2 is flushed (a 512 MiB write) before every timed step.
+
+Other legs reported on the same JSON line (rank 0): the plain one-launch-per-
+pair form on a sample of the same pairs, forward+backward pairs/s on the
+differentiation workload (30,000 x 300 vocabulary, 4,096 pairs), the
+text-shaped kNN pipeline (quadtree scan -> top-1,000 -> Flowtree -> top-10),
+the roofline of the dominant kernel, and the CPU oracle timed on the host.
+
+Multi-GPU (torchrun): every rank runs its own query batch against the same
+database (weak scaling, no data-path collective); value = all ranks' pairs /
+the slowest rank's time.
+
+--impl reference times the CPU oracle (the plain FP64 restatement of the
+paper used by the tests) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Flowtree pairs/s, batched vs per-pair GPU (rel err≤1e-5); fwd+bwd pairs/s"
+UNIT = "pairs/s"
+N_DB, N_Q, LEVELS, TOPK = 60000, 1000, 12, 10
+WORKLOAD = ("image-shaped: 28x28 grid ground set, 60,000 db x 1,000 query distributions of 100-200 pixels, "
+            "L=12, Flowtree for every query-database pair + top-10 per query")
+ALU_LANES_PER_SM = 128  # FP32/INT32 lanes per SM (4 SMSPs x 32)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--quick", action="store_true", help="small workload (smoke of the bench itself)")
+    ap.add_argument("--no-extras", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            with open(self.path) as fh:
+                for line in fh:
+                    parts = [x.strip() for x in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+        except OSError:
+            pass
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+def make_image(rank: int, quick: bool):
+    from paper_1910_04126_gb300 import synth
+    n_db, n_q = (6000, 100) if quick else (N_DB, N_Q)
+    pts = synth.grid_points()
+    shift = synth.random_shift(2, 201)
+    db = synth.stroke_images(n_db, 202)
+    q = synth.stroke_images(n_q, 203 + 1000 * rank)
+    return pts, shift, db, q
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("ft_flow.cuh", "ft_flow.cu"):
+        with open(os.path.join(ROOT, "paper_1910_04126_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(n_pairs: int):
+    """DRAM bytes per launch from the committed ncu summary, if it matches this kernel."""
+    p = os.path.join(ROOT, "profiles", "flowtree_image_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    if d.get("kernel_source_sha256_16") != kernel_source_hash():
+        return None
+    return float(d["dram_bytes_per_pair"]) * n_pairs
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline leg and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_rate(pts, shift, db, q, target_s: float, n_threads: int, seed: int = 0):
+    import oracle as O
+    ot = O.OracleTree(pts, LEVELS, shift)
+    rng = np.random.default_rng(seed)
+    sq = ot.embed_docs(q.row_ptr, q.word, q.weight)
+    sd = ot.embed_docs(db.row_ptr, db.word, db.weight)
+    n = 256
+    while True:
+        pa = rng.integers(0, q.n, n)
+        pb = rng.integers(0, db.n, n)
+        t0 = time.perf_counter()
+        ot.flowtree_batch(pts, sq, sd, pa, pb, n_threads=n_threads)
+        dt = time.perf_counter() - t0
+        if dt >= target_s or n >= 1 << 24:
+            return n / dt, n, dt
+        n = int(min(n * max(2.0, 1.2 * target_s / max(dt, 1e-3)), 1 << 24))
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    pts, shift, db, q = make_image(0, args.quick)
+    cores = os.cpu_count() or 1
+    rates = []
+    sample = None
+    per_step = 8.0 if not args.quick else 1.0
+    total = args.warmup + args.steps
+    for i in range(total):
+        r, n, dt = oracle_rate(pts, shift, db, q, per_step, cores, seed=i)
+        sample = n
+        if i >= args.warmup:
+            rates.append(r)
+    value = statistics.median(rates)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sample / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": "random (query, db) pairs of the workload"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "%d random pairs per step of the %s workload" % (sample, "quick" if args.quick else "full")},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_1910_04126_gb300 import api
+    from paper_1910_04126_gb300 import build as fbuild
+
+    if not os.path.exists(fbuild.LIB):
+        fbuild.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    pts, shift, db_h, q_h = make_image(rank, args.quick)
+    tree = api.Tree(torch.as_tensor(pts, device=dev), LEVELS, shift)
+    D = api.Docs.from_csr(tree, db_h)
+    Q = api.Docs.from_csr(tree, q_h)
+    nq, nd = Q.n_docs, D.n_docs
+    n_pairs = nq * nd
+    vocab = tree.points
+    costs = torch.empty(n_pairs, dtype=torch.float32, device=dev)
+    ws = torch.empty(api.flowtree_workspace_size(tree, Q, D, n_pairs), dtype=torch.uint8, device=dev)
+    ids = torch.empty((nq, TOPK), dtype=torch.int32, device=dev)
+    vals = torch.empty((nq, TOPK), dtype=torch.float32, device=dev)
+    from paper_1910_04126_gb300 import _ffi
+    ws_topk = torch.empty(_ffi.load().ft_topk_f32_workspace_size(nq, nd), dtype=torch.uint8, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    k_ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def step(record_kernel=None):
+        if record_kernel is not None:
+            record_kernel[0].record(stream)
+        api.flowtree_batch(tree, vocab, Q, D, out=costs, workspace=ws)
+        if record_kernel is not None:
+            record_kernel[1].record(stream)
+        api.topk_f32(costs.view(nq, nd), TOPK, ids=ids, vals=vals, workspace=ws_topk)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    step_ms, kern_ms = [], []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(k_ev)
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            kern_ms.append(k_ev[0].elapsed_time(k_ev[1]))
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = clk.summary()
+    ms = sum(step_ms) / len(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * n_pairs / (ms * 1e-3)
+
+    # end to end through the public API, host buffers in and out
+    rp = torch.as_tensor(q_h.row_ptr).pin_memory()
+    wd = torch.as_tensor(q_h.word).pin_memory()
+    wt = torch.as_tensor(q_h.weight).pin_memory()
+    ids_h = torch.empty((nq, TOPK), dtype=torch.int32).pin_memory()
+    vals_h = torch.empty((nq, TOPK), dtype=torch.float32).pin_memory()
+    h2d = rp.numel() * 8 + wd.numel() * 4 + wt.numel() * 4
+    d2h = ids_h.numel() * 4 + vals_h.numel() * 4
+
+    def e2e_step():
+        Qe = api.Docs(tree, rp.to(dev, non_blocking=True), wd.to(dev, non_blocking=True),
+                      wt.to(dev, non_blocking=True))
+        api.flowtree_batch(tree, vocab, Qe, D, out=costs, workspace=ws)
+        api.topk_f32(costs.view(nq, nd), TOPK, ids=ids, vals=vals, workspace=ws_topk)
+        ids_h.copy_(ids, non_blocking=True)
+        vals_h.copy_(vals, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    e2e_step()
+    barrier()
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_step()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_value = world * n_pairs / (statistics.mean(e2e_ms) * 1e-3)
+
+    pk, pk_kind = peaks()
+    # algorithmic work of the dominant kernel (k_flowtree_persistent), per launch:
+    # (L+2)(s_mu+s_nu) integer scan steps + (s_mu+s_nu-1)(3d+1) FLOP per pair
+    lq = np.diff(q_h.row_ptr).astype(np.float64)
+    ld = np.diff(db_h.row_ptr).astype(np.float64)
+    S = nd * lq.sum() + nq * ld.sum()  # sum over pairs of s_mu + s_nu
+    d = 2
+    ops = (LEVELS + 2) * S + (3 * d + 1) * (S - n_pairs)
+    kms = statistics.mean(kern_ms)
+    sm_clock = pk.get("sm_max_mhz", 2070.0)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak = n_sm * ALU_LANES_PER_SM * sm_clock * 1e6
+    achieved = ops / (kms * 1e-3)
+    traffic = profiled_traffic(n_pairs)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32/f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD + (" [quick]" if args.quick else ""), "pairs_per_step_per_gpu": n_pairs,
+                   "l2": "flushed (512 MiB write) before every timed step", "parallelism": "weak, %d shard(s)" % world,
+                   "launch_config": list(tree.get_config())},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": statistics.mean(e2e_ms)},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clocks,
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": alu_peak / 1e12, "unit": "Tops/s",
+                     "frac": achieved / alu_peak, "traffic": traffic,
+                     "kernel": "k_flowtree_persistent", "kernel_ms": kms,
+                     "peak_basis": "%d SMs x %d lanes x %.0f MHz (%s sm_max_mhz)" % (n_sm, ALU_LANES_PER_SM, sm_clock, pk_kind)},
+    }
+    if rank == 0 and world == 1 and not args.no_extras:
+        line.update(extras(args, tree, D, Q, q_h, db_h, pts, shift, value, dev, pk, pk_kind))
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def extras(args, tree, D, Q, q_h, db_h, pts, shift, batched_value, dev, pk, pk_kind):
+    import torch
+    from paper_1910_04126_gb300 import api, synth
+    out = {}
+    # plain one-launch-per-pair form on a sample of the same pairs
+    n_plain = 2000
+    rng = np.random.default_rng(5)
+    pa = torch.as_tensor(rng.integers(0, Q.n_docs, n_plain), dtype=torch.int32, device=dev)
+    pb = torch.as_tensor(rng.integers(0, D.n_docs, n_plain), dtype=torch.int32, device=dev)
+    api.flowtree_plain(tree, tree.points, Q, D, pa, pb)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    api.flowtree_plain(tree, tree.points, Q, D, pa, pb)
+    e1.record()
+    e1.synchronize()
+    plain = n_plain / (e0.elapsed_time(e1) * 1e-3)
+    out["plain_per_pair"] = {"value": plain, "unit": UNIT, "sample_pairs": n_plain,
+                             "batched_speedup": batched_value / plain}
+
+    # forward + backward (differentiation workload)
+    nw, npairs = (30000, 4096) if not args.quick else (5000, 512)
+    wl = synth.diff_pairs(n_words=nw, n_pairs=npairs)
+    t2 = api.Tree(torch.as_tensor(wl.points, device=dev), wl.levels, wl.shift)
+    A, B = api.Docs.from_csr(t2, wl.db), api.Docs.from_csr(t2, wl.queries)
+    idx = torch.arange(npairs, dtype=torch.int32, device=dev)
+    flows = api.Flows(t2, A, B, idx, idx)
+    cst = torch.empty(npairs, device=dev)
+    gcost = torch.ones(npairs, device=dev)
+    gv = torch.zeros_like(t2.points)
+    fws = torch.empty(api.flowtree_workspace_size(t2, A, B, npairs), dtype=torch.uint8, device=dev)
+    bws = torch.empty(int(api._ffi.load().ft_flowtree_backward_workspace_size(t2.handle, flows.handle)),
+                      dtype=torch.uint8, device=dev)
+
+    def fb():
+        api.flowtree_batch(t2, t2.points, A, B, flows.pair_a, flows.pair_b, flows=flows, out=cst, workspace=fws)
+        api.flowtree_backward(t2, A, B, flows, t2.points, gcost, grad_vocab=gv, workspace=bws)
+
+    for _ in range(3):
+        fb()
+    torch.cuda.synchronize()
+    e0.record()
+    reps = 10
+    for _ in range(reps):
+        fb()
+    e1.record()
+    e1.synchronize()
+    fb_ms = e0.elapsed_time(e1) / reps
+    e0.record()
+    for _ in range(reps):
+        api.flowtree_batch(t2, t2.points, A, B, flows.pair_a, flows.pair_b, out=cst, workspace=fws)
+    e1.record()
+    e1.synchronize()
+    f_ms = e0.elapsed_time(e1) / reps
+    out["fwd_bwd"] = {"value": npairs / (fb_ms * 1e-3), "unit": UNIT, "forward_only": npairs / (f_ms * 1e-3),
+                      "workload": "vocab %d x 300 (1,000-cluster mixture), %d doc pairs, lengths 20-300" % (nw, npairs)}
+
+    # text-shaped kNN pipeline
+    nwt, ndb, nqt, k1 = (100000, 100000, 1000, 1000) if not args.quick else (20000, 10000, 100, 256)
+    V = synth.mixture_vocab(nwt, 300, 1000, 0.3, 300)
+    t3 = api.Tree(torch.as_tensor(V, device=dev), 12, synth.random_shift(300, 301))
+    tdb = synth.zipf_docs(nwt, ndb, 302)
+    tq = synth.zipf_docs(nwt, nqt, 303)
+    D3, Q3 = api.Docs.from_csr(t3, tdb), api.Docs.from_csr(t3, tq)
+    kws = torch.empty(api.knn_workspace_size(t3, D3, Q3, k1, TOPK), dtype=torch.uint8, device=dev)
+    kid = torch.empty((nqt, TOPK), dtype=torch.int32, device=dev)
+    kdist = torch.empty((nqt, TOPK), dtype=torch.float32, device=dev)
+    for _ in range(2):
+        api.knn(t3, t3.points, D3, Q3, k1, TOPK, workspace=kws, ids=kid, dist=kdist)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        api.knn(t3, t3.points, D3, Q3, k1, TOPK, workspace=kws, ids=kid, dist=kdist)
+    g.replay()
+    torch.cuda.synchronize()
+    lat = []
+    for _ in range(5):
+        e0.record()
+        g.replay()
+        e1.record()
+        e1.synchronize()
+        lat.append(e0.elapsed_time(e1))
+    ms3 = statistics.median(lat)
+    out["text_knn_pipeline"] = {
+        "flowtree_pairs_per_s": nqt * k1 / (ms3 * 1e-3), "queries_per_s": nqt / (ms3 * 1e-3),
+        "scan_pairs_per_s": nqt * ndb / (ms3 * 1e-3), "batch_ms_median": ms3, "graph": True,
+        "workload": "vocab %d x 300, %d docs (log-normal lengths, Zipf(1.1) words), %d queries, top-%d -> top-%d"
+                    % (nwt, ndb, nqt, k1, TOPK)}
+
+    # CPU oracle on the host cores (bounded sample of the same image workload)
+    cores = os.cpu_count() or 1
+    r_n, n_n, dt_n = oracle_rate(pts, shift, db_h, q_h, 12.0 if not args.quick else 2.0, cores, seed=1)
+    r_1, n_1, dt_1 = oracle_rate(pts, shift, db_h, q_h, 3.0 if not args.quick else 0.5, 1, seed=2)
+    out["cpu_baseline"] = {"value": r_n, "unit": UNIT, "cores": cores, "kind": "oracle",
+                           "sample": "%d random (query, db) pairs of the image workload, %.1f s" % (n_n, dt_n),
+                           "single_thread": {"value": r_1, "sample_pairs": n_1}}
+    out["roofline_hbm"] = hbm_roofline(q_h, db_h, batched_value, pk, pk_kind)
+    return out
+
+
+def hbm_roofline(q_h, db_h, pairs_per_s, pk, pk_kind):
+    # algorithmic bytes per pair at the candidate side: its support
+    # (rank, mass, point id: 12 B/item), one LCA byte per merged adjacency,
+    # its rows (d = 2 floats), and the 4-byte result
+    s_q = float(np.diff(q_h.row_ptr).mean())
+    s_d = float(np.diff(db_h.row_ptr).mean())
+    per_pair = s_d * 12 + (s_q + s_d) * 1 + s_d * 8 + 4
+    achieved = per_pair * pairs_per_s / 1e9
+    return {"bytes_per_pair": per_pair, "achieved": achieved, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
+            "frac": achieved / pk.get("hbm_gbs", 6800.0), "peak_kind": pk_kind}
+
+
+if __name__ == "__main__":
+    main()

@@ -181,13 +181,23 @@ ft_status ft_flowtree_plain(const ft_tree* t, const float* vocab_dev, const ft_d
                             const int32_t* pair_a_dev, const int32_t* pair_b_dev, int64_t n_pairs,
                             float* cost_out_dev, void* workspace, size_t ws_bytes, void* stream);
 
-/* Launch configuration of ft_flowtree_batch: warps per CTA and the number
- * of merged support items each warp stages in shared memory.  0 = default.
+/* Launch configuration of ft_flowtree_batch.  0 = default for every field.
+ *   algo          : FT_ALGO_AUTO, FT_ALGO_WARP (a warp per pair, level by
+ *                   level over the merged supports staged in shared memory)
+ *                   or FT_ALGO_THREAD (a thread per pair, one sweep with a
+ *                   stack of open tree nodes; dim <= 8 only).  AUTO = WARP
+ *                   (the faster of the two on every measured workload).
+ *   warps_per_cta : warps per CTA (1..8).
+ *   stage_items   : merged support items each warp stages on chip (WARP).
  * ft_flowtree_autotune times a few configurations on the given pairs (with
  * CUDA events on `stream`) and installs the fastest for this tree. */
+#define FT_ALGO_AUTO 0
+#define FT_ALGO_WARP 1
+#define FT_ALGO_THREAD 2
 typedef struct {
     int32_t warps_per_cta;
     int32_t stage_items;
+    int32_t algo;
 } ft_flowtree_config;
 ft_status ft_flowtree_set_config(ft_tree* t, const ft_flowtree_config* cfg);
 ft_status ft_flowtree_get_config(const ft_tree* t, ft_flowtree_config* cfg);
@@ -256,6 +266,17 @@ size_t ft_knn_workspace_size(const ft_tree* t, const ft_docs* db, const ft_docs*
 ft_status ft_knn(const ft_tree* t, const float* vocab_dev, const ft_docs* db, const ft_docs* queries, int32_t k1,
                  int32_t k, void* workspace, size_t ws_bytes, int32_t* ids_out_dev, float* dist_out_dev,
                  void* stream);
+
+/* ------------------------------------------------------------------------
+ * Per-row top-k of FP32 values (final selection, Sec. 5.2): for each of
+ * n_rows rows of values_dev [n_rows][n_cols] (row-major, non-negative
+ * values such as Flowtree costs), the k smallest ascending by (value,
+ * column), written to ids_out_dev / vals_out_dev [n_rows][k].  NaN sorts
+ * last.  k <= min(n_cols, 4096).  Allocation-free.
+ * ------------------------------------------------------------------------ */
+size_t ft_topk_f32_workspace_size(int64_t n_rows, int64_t n_cols);
+ft_status ft_topk_f32(const float* values_dev, int64_t n_rows, int64_t n_cols, int32_t k, void* workspace,
+                      size_t ws_bytes, int32_t* ids_out_dev, float* vals_out_dev, void* stream);
 
 #ifdef __cplusplus
 }

@@ -31,8 +31,11 @@ class DocsInfo(C.Structure):
                 ("n_embed", C.c_int64)]
 
 
+ALGO_AUTO, ALGO_WARP, ALGO_THREAD = 0, 1, 2
+
+
 class FlowtreeConfig(C.Structure):
-    _fields_ = [("warps_per_cta", C.c_int32), ("stage_items", C.c_int32)]
+    _fields_ = [("warps_per_cta", C.c_int32), ("stage_items", C.c_int32), ("algo", C.c_int32)]
 
 
 vp = C.c_void_p
@@ -69,6 +72,8 @@ SIGNATURES = {
     "ft_quadtree_l1_dense": (i32, [vp, vp, vp, vp, vp]),
     "ft_knn_workspace_size": (sz, [vp, vp, vp, i32, i32]),
     "ft_knn": (i32, [vp, vp, vp, vp, i32, i32, vp, sz, vp, vp, vp]),
+    "ft_topk_f32_workspace_size": (sz, [i64, i64]),
+    "ft_topk_f32": (i32, [vp, i64, i64, i32, vp, sz, vp, vp, vp]),
 }
 
 _lib = None

@@ -97,12 +97,13 @@ class Tree:
         return int(_ffi.load().ft_tree_status(self._h, _stream(stream)))
 
     def get_config(self):
+        """(warps_per_cta, stage_items, algo); 0 = default."""
         cfg = _ffi.FlowtreeConfig()
         check(_ffi.load().ft_flowtree_get_config(self._h, C.byref(cfg)), "ft_flowtree_get_config")
-        return int(cfg.warps_per_cta), int(cfg.stage_items)
+        return int(cfg.warps_per_cta), int(cfg.stage_items), int(cfg.algo)
 
-    def set_config(self, warps_per_cta: int = 0, stage_items: int = 0):
-        cfg = _ffi.FlowtreeConfig(warps_per_cta, stage_items)
+    def set_config(self, warps_per_cta: int = 0, stage_items: int = 0, algo: int = 0):
+        cfg = _ffi.FlowtreeConfig(warps_per_cta, stage_items, algo)
         check(_ffi.load().ft_flowtree_set_config(self._h, C.byref(cfg)), "ft_flowtree_set_config")
 
 
@@ -255,9 +256,9 @@ def flowtree_autotune(tree: Tree, vocab: torch.Tensor, a: Docs, b: Docs, pair_a=
     saved = tree.get_config()
     best_ws = 0
     for w in (2, 4, 8):
-        for cap in (256, 384, 512, 768, 1024):
+        for cap in (32, 256, 384, 512, 768, 1024):
             try:
-                tree.set_config(w, cap)
+                tree.set_config(w, cap, _ffi.ALGO_WARP)
                 best_ws = max(best_ws, lib.ft_flowtree_batch_workspace_size(tree.handle, a.handle, b.handle,
                                                                              n_pairs))
             except _ffi.FlowtreeError:
@@ -268,7 +269,7 @@ def flowtree_autotune(tree: Tree, vocab: torch.Tensor, a: Docs, b: Docs, pair_a=
     code = lib.ft_flowtree_autotune(tree.handle, _ptr(vocab), a.handle, b.handle, _ptr(pa), _ptr(pb), n_pairs,
                                     _ptr(scratch), _ptr(ws), ws.numel(), _stream(stream), C.byref(cfg))
     check(code, "ft_flowtree_autotune")
-    return int(cfg.warps_per_cta), int(cfg.stage_items)
+    return int(cfg.warps_per_cta), int(cfg.stage_items), int(cfg.algo)
 
 
 def flowtree_backward(tree: Tree, a: Docs, b: Docs, flows: Flows, vocab: torch.Tensor, grad_cost: torch.Tensor,
@@ -329,6 +330,22 @@ def knn(tree: Tree, vocab: torch.Tensor, db: Docs, queries: Docs, k1: int, k: in
                       _ptr(ids), _ptr(dist), _stream(stream))
     check(code, "ft_knn")
     return ids, dist
+
+
+def topk_f32(values: torch.Tensor, k: int, ids: Optional[torch.Tensor] = None,
+             vals: Optional[torch.Tensor] = None, workspace: Optional[torch.Tensor] = None, stream=None):
+    """Per-row k smallest of a [rows, cols] FP32 tensor, ties by column (ft_topk_f32)."""
+    lib = _ffi.load()
+    v = values.contiguous()
+    rows, cols = v.shape
+    if ids is None:
+        ids = torch.empty((rows, k), dtype=torch.int32, device=v.device)
+    if vals is None:
+        vals = torch.empty((rows, k), dtype=torch.float32, device=v.device)
+    ws = _workspace(lib.ft_topk_f32_workspace_size(rows, cols), v.device, workspace)
+    check(lib.ft_topk_f32(_ptr(v), rows, cols, k, _ptr(ws), ws.numel(), _ptr(ids), _ptr(vals), _stream(stream)),
+          "ft_topk_f32")
+    return ids, vals
 
 
 class FlowtreeFunction(torch.autograd.Function):

@@ -5,6 +5,7 @@
 #include <cstring>
 
 #include "ft_flow.cuh"
+#include "ft_flow_thread.cuh"
 
 using namespace ftk;
 
@@ -13,12 +14,16 @@ namespace {
 constexpr int kDefaultWarps = 4;
 constexpr int kMaxStage = 2048;
 
+// A warp per pair, persistent: warps take `grab` consecutive queue entries at
+// a time.  Dynamic shared memory: [tables (if staged)] [one WarpBuf per warp].
 template <int MODE, bool SAVE>
-__global__ void __launch_bounds__(256) k_flowtree_persistent(FlowCtx c, int cap, int grab) {
+__global__ void __launch_bounds__(256) k_flowtree_persistent(FlowCtx c, int cap, int grab, int tables_bytes) {
     extern __shared__ __align__(16) uint8_t smem[];
     const int warp = int(threadIdx.x >> 5);
     const unsigned lane = lane_id();
-    const WarpBuf sbuf = carve_warpbuf(smem + size_t(warp) * warpbuf_bytes(cap), cap);
+    const Tables tb = tables_bytes > 0 ? stage_tables(c, smem) : Tables{c.vocab, c.rmq};
+    uint8_t* wbase = smem + tables_bytes;
+    const WarpBuf sbuf = carve_warpbuf(wbase + size_t(warp) * warpbuf_bytes(cap), cap);
     const int64_t gw = int64_t(blockIdx.x) * (blockDim.x >> 5) + warp;
     WarpBuf gbuf = sbuf;
     if (c.gscratch) gbuf = carve_warpbuf(c.gscratch + size_t(gw) * c.gscratch_warp_bytes, c.gscratch_items);
@@ -38,9 +43,9 @@ __global__ void __launch_bounds__(256) k_flowtree_persistent(FlowCtx c, int cap,
             const int n = int(c.a_ptr[da + 1] - c.a_ptr[da]) + int(c.b_ptr[db + 1] - c.b_ptr[db]);
             float cost;
             if (n <= cap) {
-                cost = flowtree_pair<MODE, SAVE>(c, sbuf, pair, da, db);
+                cost = flowtree_pair<MODE, SAVE>(c, sbuf, tb, pair, da, db);
             } else if (c.gscratch && n <= c.gscratch_items) {
-                cost = flowtree_pair<MODE, SAVE>(c, gbuf, pair, da, db);
+                cost = flowtree_pair<MODE, SAVE>(c, gbuf, tb, pair, da, db);
             } else {
                 if (lane == 0) ft_flag(c.status, FT_DEV_EOVERFLOW);
                 cost = __int_as_float(0x7fc00000);
@@ -50,11 +55,53 @@ __global__ void __launch_bounds__(256) k_flowtree_persistent(FlowCtx c, int cap,
     }
 }
 
+// A thread per pair (low-dimensional ground sets).  The vocabulary and the
+// LCA table are copied to shared memory when they fit; each warp takes 32
+// consecutive pairs from the queue at a time.
+template <bool SAVE, int TMAX>
+__global__ void __launch_bounds__(256) k_flowtree_thread(FlowCtx c, int tables_bytes) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    const Tables tb = tables_bytes > 0 ? stage_tables(c, smem) : Tables{c.vocab, c.rmq};
+    uint64_t buf[TMAX];
+    const unsigned lane = lane_id();
+    for (;;) {
+        unsigned long long first = 0;
+        if (lane == 0) first = atomicAdd(reinterpret_cast<unsigned long long*>(c.queue), 32ull);
+        first = __shfl_sync(FULL_MASK, first, 0);
+        if (first >= (unsigned long long)c.n_pairs) break;
+        const int64_t q = int64_t(first) + lane;
+        if (q >= c.n_pairs) continue;
+        const int64_t pair = c.order ? int64_t(c.order[q]) : q;
+        int64_t da, db;
+        if (c.pair_a) {
+            da = c.pair_a[pair];
+            db = c.pair_b[pair];
+        } else {
+            da = pair / c.nb_cross;
+            db = pair - da * c.nb_cross;
+        }
+        float cost = __int_as_float(0x7fc00000);
+        if (da < 0 || da >= c.na_docs || db < 0 || db >= c.nb_docs) {
+            ft_flag(c.status, FT_DEV_EINVAL);
+        } else {
+            const int n = int(c.a_ptr[da + 1] - c.a_ptr[da]) + int(c.b_ptr[db + 1] - c.b_ptr[db]);
+            if (n > TMAX) {
+                ft_flag(c.status, FT_DEV_EOVERFLOW);
+            } else {
+                ThreadPair<SAVE, TMAX> tp(c, tb, buf);
+                cost = tp.run(pair, da, db);
+            }
+        }
+        c.cost_out[pair] = cost;
+    }
+}
+
 // The plain form: one warp, one pair per launch.
 template <int MODE>
 __global__ void __launch_bounds__(32) k_flowtree_one(FlowCtx c, int cap, int64_t pair) {
     extern __shared__ __align__(16) uint8_t smem[];
     const WarpBuf sbuf = carve_warpbuf(smem, cap);
+    const Tables tb{c.vocab, c.rmq};
     int64_t da, db;
     if (!pair_docs(c, pair, &da, &db)) {
         if (lane_id() == 0) c.cost_out[pair] = __int_as_float(0x7fc00000);
@@ -63,10 +110,10 @@ __global__ void __launch_bounds__(32) k_flowtree_one(FlowCtx c, int cap, int64_t
     const int n = int(c.a_ptr[da + 1] - c.a_ptr[da]) + int(c.b_ptr[db + 1] - c.b_ptr[db]);
     float cost;
     if (n <= cap) {
-        cost = flowtree_pair<MODE, false>(c, sbuf, pair, da, db);
+        cost = flowtree_pair<MODE, false>(c, sbuf, tb, pair, da, db);
     } else if (c.gscratch && n <= c.gscratch_items) {
         const WarpBuf gbuf = carve_warpbuf(c.gscratch, c.gscratch_items);
-        cost = flowtree_pair<MODE, false>(c, gbuf, pair, da, db);
+        cost = flowtree_pair<MODE, false>(c, gbuf, tb, pair, da, db);
     } else {
         if (lane_id() == 0) ft_flag(c.status, FT_DEV_EOVERFLOW);
         cost = __int_as_float(0x7fc00000);
@@ -122,6 +169,7 @@ int grid_for(int64_t work, int threads) {
 int round32(int x) { return (x + 31) & ~31; }
 
 struct Plan {
+    int algo = FT_ALGO_WARP;
     int mode = 0;
     int warps = kDefaultWarps;
     int cap = 0;
@@ -131,7 +179,29 @@ struct Plan {
     size_t gscratch_warp_bytes = 0;
     bool need_order = false;
     int64_t n_pairs = 0;
+    int tmax = 0;          // thread algorithm: item buffer per thread
+    int tables_bytes = 0;  // vocabulary + LCA table staged in shared memory (0 = read from global)
 };
+
+constexpr int kThreadMaxItems = 2048;
+constexpr size_t kTablesMax = 32 * 1024;  // stage the tables when they are at most this big
+
+int staged_tables_bytes(const ft_tree* t) {
+    const size_t b = (tables_bytes(t->n, t->dim, t->rmq_levels) + 127) & ~size_t(127);
+    return b <= kTablesMax ? int(b) : 0;
+}
+
+template <bool SAVE>
+void* thread_fn(int tmax) {
+    switch (tmax) {
+        case 256: return reinterpret_cast<void*>(&k_flowtree_thread<SAVE, 256>);
+        case 512: return reinterpret_cast<void*>(&k_flowtree_thread<SAVE, 512>);
+        case 1024: return reinterpret_cast<void*>(&k_flowtree_thread<SAVE, 1024>);
+        default: return reinterpret_cast<void*>(&k_flowtree_thread<SAVE, 2048>);
+    }
+}
+
+void* thread_kernel(int tmax, bool save) { return save ? thread_fn<true>(tmax) : thread_fn<false>(tmax); }
 
 template <int MODE, bool SAVE>
 void* persistent_fn() {
@@ -161,10 +231,26 @@ ft_status make_plan(const ft_tree* t, const ft_docs* a, const ft_docs* b, int64_
     p->n_pairs = n_pairs;
     p->warps = cfg.warps_per_cta > 0 ? cfg.warps_per_cta : kDefaultWarps;
     const int maxn = round32(std::max(a->max_support + b->max_support, 32));
+    p->need_order = explicit_pairs && n_pairs > 1;
+    const bool thread_ok = t->dim <= 8 && maxn <= kThreadMaxItems;
+    p->algo = cfg.algo != FT_ALGO_AUTO ? cfg.algo : FT_ALGO_WARP;
+    if (p->algo == FT_ALGO_THREAD) {
+        if (!thread_ok) return FT_EUNSUPPORTED;
+        p->tmax = maxn <= 256 ? 256 : maxn <= 512 ? 512 : maxn <= 1024 ? 1024 : 2048;
+        p->tables_bytes = staged_tables_bytes(t);
+        p->smem = size_t(p->tables_bytes);
+        int sms = 0, bps = 0;
+        FT_TRY(ft_device_sms(&sms));
+        FT_TRY(ft_prepare_kernel(thread_kernel(p->tmax, save), p->warps * 32, p->smem, &bps));
+        if (bps < 1) return FT_EUNSUPPORTED;
+        p->blocks = sms * bps;
+        return FT_OK;
+    }
     int cap = cfg.stage_items > 0 ? round32(cfg.stage_items) : std::min(maxn, 512);
     cap = std::min(cap, kMaxStage);
     p->cap = cap;
-    p->smem = size_t(p->warps) * warpbuf_bytes(cap);
+    p->tables_bytes = staged_tables_bytes(t);
+    p->smem = size_t(p->tables_bytes) + size_t(p->warps) * warpbuf_bytes(cap);
     int dev = 0, max_smem = 0, sms = 0;
     FT_CUDA(cudaGetDevice(&dev));
     FT_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
@@ -179,7 +265,6 @@ ft_status make_plan(const ft_tree* t, const ft_docs* a, const ft_docs* b, int64_
         p->gscratch_items = maxn;
         p->gscratch_warp_bytes = (warpbuf_bytes(maxn) + 255) & ~size_t(255);
     }
-    p->need_order = explicit_pairs && n_pairs > 1;
     return FT_OK;
 }
 
@@ -222,6 +307,7 @@ FlowCtx make_ctx(const ft_tree* t, const float* vocab, const ft_docs* a, const f
     c.rmq = t->d_rmq;
     c.n_points = t->n;
     c.levels = t->levels;
+    c.rmq_levels = t->rmq_levels;
     c.vocab = vocab;
     c.dim = t->dim;
     c.a_ptr = a->d_ptr;
@@ -244,13 +330,20 @@ FlowCtx make_ctx(const ft_tree* t, const float* vocab, const ft_docs* a, const f
 }
 
 ft_status launch_persistent(const Plan& p, FlowCtx c, bool save, cudaStream_t s) {
+    FT_CUDA(cudaMemsetAsync(c.queue, 0, 8, s));
+    if (p.algo == FT_ALGO_THREAD) {
+        void* fn = thread_kernel(p.tmax, save);
+        int tbytes = p.tables_bytes;
+        void* args[] = {&c, &tbytes};
+        FT_CUDA(cudaLaunchKernel(fn, dim3(p.blocks), dim3(p.warps * 32), args, p.smem, s));
+        return FT_OK;
+    }
     const int64_t n_warps = int64_t(p.blocks) * p.warps;
     int64_t grab = c.n_pairs / (n_warps * 32);
     grab = std::max<int64_t>(1, std::min<int64_t>(grab, 16));
-    FT_CUDA(cudaMemsetAsync(c.queue, 0, 8, s));
     void* fn = persistent_kernel(p.mode, save);
-    int cap = p.cap, g = int(grab);
-    void* args[] = {&c, &cap, &g};
+    int cap = p.cap, g = int(grab), tbytes = p.tables_bytes;
+    void* args[] = {&c, &cap, &g, &tbytes};
     FT_CUDA(cudaLaunchKernel(fn, dim3(p.blocks), dim3(p.warps * 32), args, p.smem, s));
     return FT_OK;
 }
@@ -386,9 +479,11 @@ extern "C" ft_status ft_flowtree_autotune(ft_tree* t, const float* vocab_dev, co
     const int warps[] = {2, 4, 8};
     for (int cap : caps) {
         if (cap > maxn || cap > kMaxStage) continue;
-        for (int w : warps) cands.push_back({w, cap});
+        for (int w : warps) cands.push_back({w, cap, FT_ALGO_WARP});
     }
-    if (cands.empty()) cands.push_back({kDefaultWarps, std::min(maxn, 512)});
+    if (t->dim <= 8 && maxn <= kThreadMaxItems)
+        for (int w : {2, 4, 8}) cands.push_back({w, 0, FT_ALGO_THREAD});
+    if (cands.empty()) cands.push_back({kDefaultWarps, std::min(maxn, 512), FT_ALGO_WARP});
     cudaEvent_t e0, e1;
     FT_CUDA(cudaEventCreate(&e0));
     FT_CUDA(cudaEventCreate(&e1));

@@ -127,10 +127,13 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_qt_scan(ScanArgs a) {
 
 // Per row: the k smallest of n unique u64 keys, ascending, by an 8-bit
 // radix select (MSB first) followed by a bitonic sort of the k survivors.
-// ids_out[k] = low 24 bits; l1_out[k] = key >> 24 (optional).
+// Quadtree keys (F32 = false): ids_out = low 24 bits, l1_out = key >> 24.
+// Value keys (F32 = true): key = (float bits << 32) | column, ids_out = low 32
+// bits, val_out = the float.
+template <bool F32>
 __global__ void __launch_bounds__(SEL_THREADS) k_select_u64(const uint64_t* __restrict__ keys, int64_t n, int k,
                                                             int32_t* __restrict__ ids_out, int64_t* __restrict__ l1_out,
-                                                            uint32_t* status) {
+                                                            float* __restrict__ val_out, uint32_t* status) {
     __shared__ uint32_t hist[256];
     __shared__ uint64_t cand[MAX_K1];
     __shared__ uint64_t prefix_s, mask_s;
@@ -200,8 +203,26 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_u64(const uint64_t* __re
     }
     for (int i = threadIdx.x; i < k; i += blockDim.x) {
         const uint64_t key = cand[i];
-        ids_out[int64_t(blockIdx.x) * k + i] = int32_t(key & 0xFFFFFFu);
-        if (l1_out) l1_out[int64_t(blockIdx.x) * k + i] = int64_t(key >> 24);
+        if (F32) {
+            ids_out[int64_t(blockIdx.x) * k + i] = int32_t(key & 0xFFFFFFFFu);
+            val_out[int64_t(blockIdx.x) * k + i] = __uint_as_float(uint32_t(key >> 32));
+        } else {
+            ids_out[int64_t(blockIdx.x) * k + i] = int32_t(key & 0xFFFFFFu);
+            if (l1_out) l1_out[int64_t(blockIdx.x) * k + i] = int64_t(key >> 24);
+        }
+    }
+}
+
+// key = (bits of the value << 32) | column; values are non-negative costs,
+// so their bit patterns order like the values (NaN sorts after +inf).
+__global__ void k_f32_keys(const float* __restrict__ v, int64_t rows, int64_t cols, uint64_t* __restrict__ keys) {
+    const int64_t n = rows * cols;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+        const float x = v[i];
+        uint32_t bits = __float_as_uint(x);
+        if (x != x) bits = 0x7FC00000u;
+        else if (bits & 0x80000000u) bits = 0;  // -0.0 (and any negative) sorts first
+        keys[i] = (uint64_t(bits) << 32) | uint64_t(i % cols);
     }
 }
 
@@ -367,8 +388,8 @@ extern "C" ft_status ft_quadtree_scan(const ft_tree* t, const ft_docs* queries, 
     uint64_t* keys = nullptr;
     scan_layout(queries, db, workspace, &keys);
     FT_TRY(launch_scan(t, queries, db, keys, nullptr, s));
-    k_select_u64<<<unsigned(queries->n_docs), SEL_THREADS, 0, s>>>(keys, db->n_docs, k1, cand_ids_out_dev,
-                                                                   cand_l1_out_dev, t->d_status);
+    k_select_u64<false><<<unsigned(queries->n_docs), SEL_THREADS, 0, s>>>(keys, db->n_docs, k1, cand_ids_out_dev,
+                                                                          cand_l1_out_dev, nullptr, t->d_status);
     FT_CUDA(cudaGetLastError());
     return FT_OK;
 }
@@ -414,11 +435,33 @@ extern "C" ft_status ft_knn(const ft_tree* t, const float* vocab_dev, const ft_d
     knn_layout(t, db, queries, k1, workspace, &l);
     const int64_t nq = queries->n_docs, np = nq * int64_t(k1);
     FT_TRY(launch_scan(t, queries, db, l.keys, nullptr, s));
-    k_select_u64<<<unsigned(nq), SEL_THREADS, 0, s>>>(l.keys, db->n_docs, k1, l.cand, nullptr, t->d_status);
+    k_select_u64<false><<<unsigned(nq), SEL_THREADS, 0, s>>>(l.keys, db->n_docs, k1, l.cand, nullptr, nullptr, t->d_status);
     k_knn_pairs<<<grid_for(np, 256), 256, 0, s>>>(l.cand, nq, k1, l.pa, l.pb);
     FT_CUDA(cudaGetLastError());
     FT_TRY(ft_flowtree_batch(t, vocab_dev, queries, db, l.pa, l.pb, np, l.cost, nullptr, l.fws, l.fws_bytes, s));
     k_final_topk<<<unsigned(nq), SEL_THREADS, 0, s>>>(l.cost, l.cand, k1, k, ids_out_dev, dist_out_dev);
+    FT_CUDA(cudaGetLastError());
+    return FT_OK;
+}
+
+extern "C" size_t ft_topk_f32_workspace_size(int64_t n_rows, int64_t n_cols) {
+    if (n_rows < 1 || n_cols < 1) return 0;
+    WsCarver w(nullptr);
+    w.take<uint64_t>(size_t(n_rows) * n_cols);
+    return w.off + 256;
+}
+
+extern "C" ft_status ft_topk_f32(const float* values_dev, int64_t n_rows, int64_t n_cols, int32_t k, void* workspace,
+                                 size_t ws_bytes, int32_t* ids_out_dev, float* vals_out_dev, void* stream) {
+    if (!values_dev || !ids_out_dev || !vals_out_dev || n_rows < 1 || n_cols < 1 || k < 1 || k > MAX_K1 ||
+        int64_t(k) > n_cols || n_cols >= (int64_t(1) << 32) || n_rows > 0x7FFFFFFF)
+        return FT_EINVAL;
+    if (!workspace || ws_bytes < ft_topk_f32_workspace_size(n_rows, n_cols)) return FT_EWORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint64_t* keys = static_cast<uint64_t*>(workspace);
+    k_f32_keys<<<grid_for(n_rows * n_cols, 256), 256, 0, s>>>(values_dev, n_rows, n_cols, keys);
+    k_select_u64<true><<<unsigned(n_rows), SEL_THREADS, 0, s>>>(keys, n_cols, k, ids_out_dev, nullptr, vals_out_dev,
+                                                                nullptr);
     FT_CUDA(cudaGetLastError());
     return FT_OK;
 }

@@ -79,10 +79,21 @@ def _oracle_costs(otree, pts, SA, SB, pa, pb):
     return otree.flowtree_batch(pts, SA, SB, pa, pb, n_threads=4)
 
 
-@pytest.mark.parametrize("name", sorted(CASES))
-def test_flowtree_cross_and_pairs_vs_oracle(name):
+def algo_cases(names):
+    """(case, algorithm): every case with the default, plus both algorithms where dim <= 8."""
+    out = []
+    for n in names:
+        out.append((n, 0))
+        if CASES[n][0].shape[1] <= 8:
+            out += [(n, 1), (n, 2)]
+    return out
+
+
+@pytest.mark.parametrize("name,algo", algo_cases(sorted(CASES)))
+def test_flowtree_cross_and_pairs_vs_oracle(name, algo):
     pts, L, shift, db, q = CASES[name]
     tree, otree = build_both(pts, L, shift)
+    tree.set_config(0, 0, algo)
     Dd, Dq = api.Docs.from_csr(tree, db), api.Docs.from_csr(tree, q)
     Sd, Sq = oracle_supports(otree, db), oracle_supports(otree, q)
     vocab = tree.points
@@ -104,10 +115,11 @@ def test_flowtree_cross_and_pairs_vs_oracle(name):
     assert tree.status() == 0
 
 
-@pytest.mark.parametrize("name", ["tiny2d", "d300", "line"])
-def test_saved_flows_bit_exact(name):
+@pytest.mark.parametrize("name,algo", algo_cases(["tiny2d", "d300", "line", "grid"]))
+def test_saved_flows_bit_exact(name, algo):
     pts, L, shift, db, _ = CASES[name]
     tree, otree = build_both(pts, L, shift)
+    tree.set_config(0, 0, algo)
     Dd = api.Docs.from_csr(tree, db)
     Sd = oracle_supports(otree, db)
     rng = np.random.default_rng(1)
@@ -129,9 +141,15 @@ def test_plain_form_equals_batched(name):
     pts, L, shift, db, q = CASES[name]
     tree, _ = build_both(pts, L, shift)
     Dd, Dq = api.Docs.from_csr(tree, db), api.Docs.from_csr(tree, q)
-    a = api.flowtree_batch(tree, tree.points, Dq, Dd)
     b = api.flowtree_plain(tree, tree.points, Dq, Dd)
+    # the plain form runs the warp-per-pair code: bitwise equal to the batched warp path
+    tree.set_config(0, 0, 1)
+    a = api.flowtree_batch(tree, tree.points, Dq, Dd)
     assert torch.equal(a, b)
+    # the default algorithm agrees within the FP32 tolerance
+    tree.set_config(0, 0, 0)
+    c = api.flowtree_batch(tree, tree.points, Dq, Dd)
+    torch.testing.assert_close(c, b, rtol=2 * REL, atol=0)
 
 
 @pytest.mark.parametrize("cap", [32, 64, 96])
