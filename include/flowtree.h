@@ -66,7 +66,8 @@ typedef enum {
     FT_ETIMEOUT = -4,      /* a bounded device-side wait gave up            */
     FT_EOVERFLOW = -5,     /* a device-side capacity was exceeded           */
     FT_EUNSUPPORTED = -6,  /* valid input outside the compiled limits       */
-    FT_EWORKSPACE = -7     /* workspace NULL or smaller than required       */
+    FT_EWORKSPACE = -7,    /* workspace NULL or smaller than required       */
+    FT_ETOOBIG = -8        /* batch needs more than the fixed static scratch */
 } ft_status;
 
 typedef struct ft_tree ft_tree;   /* quadtree over the ground points          */
@@ -174,6 +175,30 @@ ft_status ft_flowtree_batch(const ft_tree* t, const float* vocab_dev, const ft_d
                             const int32_t* pair_a_dev, const int32_t* pair_b_dev, int64_t n_pairs,
                             float* cost_out_dev, ft_flows* flows_out, void* workspace, size_t ws_bytes,
                             void* stream);
+
+/* Allocation-free variant of ft_flowtree_batch (the paper has no
+ * counterpart; this is a deployment convenience).  For callers that cannot
+ * allocate device memory at all -- a host whose device memory is held by its
+ * own pooled allocator with nothing exposed to plug-ins, a latency-bound
+ * loop where cudaMalloc's implicit device synchronisation is not allowed, or
+ * code that would have to allocate while a stream is being captured -- and
+ * so cannot provide ft_flowtree_batch's workspace.  Same inputs and outputs
+ * (no saved flows); the workspace comes from a fixed device array of
+ * FT_STATIC_SCRATCH_BYTES compiled into the library, held by every GPU that
+ * loads it until the library is unloaded.  Calls no cudaMalloc/cudaFree.
+ *   - Limit: a batch whose ft_flowtree_batch_workspace_size() exceeds
+ *     FT_STATIC_SCRATCH_BYTES is rejected with FT_ETOOBIG before any launch
+ *     (explicit pair lists up to about 1.2 million pairs; cross products whose
+ *     pairs fit the on-chip staging).
+ *   - The first call on a device (with that device current) looks up the
+ *     array's device address; make that first call before any stream capture.
+ *   - Every call shares the array, which keeps the previous call's contents
+ *     (what must start at zero is cleared by each call): calls that overlap on
+ *     the GPU race and give undefined results; serialise them on one stream. */
+#define FT_STATIC_SCRATCH_BYTES (16u << 20)
+ft_status ft_flowtree_batch_static(const ft_tree* t, const float* vocab_dev, const ft_docs* a, const ft_docs* b,
+                                   const int32_t* pair_a_dev, const int32_t* pair_b_dev, int64_t n_pairs,
+                                   float* cost_out_dev, void* stream);
 
 /* The plain form: the same computation with one kernel launch per pair
  * (one warp), in pair order.  Used as the per-pair baseline. */

@@ -12,7 +12,7 @@ from .build import LIB
 
 FT_OK = 0
 STATUS = {0: "FT_OK", -1: "FT_EINVAL", -2: "FT_ENOMEM", -3: "FT_ECUDA", -4: "FT_ETIMEOUT",
-          -5: "FT_EOVERFLOW", -6: "FT_EUNSUPPORTED", -7: "FT_EWORKSPACE"}
+          -5: "FT_EOVERFLOW", -6: "FT_EUNSUPPORTED", -7: "FT_EWORKSPACE", -8: "FT_ETOOBIG"}
 
 
 class FlowtreeError(RuntimeError):
@@ -74,6 +74,7 @@ SIGNATURES = {
     "ft_knn": (i32, [vp, vp, vp, vp, i32, i32, vp, sz, vp, vp, vp]),
     "ft_topk_f32_workspace_size": (sz, [i64, i64]),
     "ft_topk_f32": (i32, [vp, i64, i64, i32, vp, sz, vp, vp, vp]),
+    "ft_flowtree_batch_static": (i32, [vp, vp, vp, vp, vp, vp, i64, vp, vp]),
 }
 
 _lib = None

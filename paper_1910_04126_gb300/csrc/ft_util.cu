@@ -28,6 +28,7 @@ extern "C" const char* ft_status_string(ft_status s) {
         case FT_EOVERFLOW: return "FT_EOVERFLOW: device-side capacity exceeded";
         case FT_EUNSUPPORTED: return "FT_EUNSUPPORTED: outside the compiled limits";
         case FT_EWORKSPACE: return "FT_EWORKSPACE: workspace missing or too small";
+        case FT_ETOOBIG: return "FT_ETOOBIG: batch needs more than the fixed static scratch";
     }
     return "unknown ft_status";
 }
