@@ -63,7 +63,25 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true", help="small workload (smoke of the bench itself)")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--profile-case", nargs=2, type=int, metavar=("N_DB", "N_Q"),
+                    help="only run the image-shaped batch N_Q x N_DB three times (a case for ncu); no timing")
+    ap.add_argument("--config", default="0,0,0", help="warps_per_cta,stage_items,algo for --profile-case")
     return ap.parse_args()
+
+
+def profile_case(args):
+    import torch
+    from paper_1910_04126_gb300 import api, synth
+    n_db, n_q = args.profile_case
+    db, q = synth.stroke_images(n_db, 202), synth.stroke_images(n_q, 203)
+    tree = api.Tree(torch.as_tensor(synth.grid_points(), device="cuda"), LEVELS, synth.random_shift(2, 201))
+    tree.set_config(*[int(x) for x in args.config.split(",")])
+    D, Q = api.Docs.from_csr(tree, db), api.Docs.from_csr(tree, q)
+    out = torch.empty(n_db * n_q, device="cuda")
+    for _ in range(3):
+        api.flowtree_batch(tree, tree.points, Q, D, out=out)
+    torch.cuda.synchronize()
+    print("profile case done: %d pairs, config %s, status %d" % (n_db * n_q, args.config, tree.status()))
 
 
 # ---------------------------------------------------------------------------
@@ -214,6 +232,9 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
+    if args.profile_case:
+        profile_case(args)
+        return
 
     import torch
     import torch.distributed as dist
@@ -235,6 +256,10 @@ def main():
     tree = api.Tree(torch.as_tensor(pts, device=dev), LEVELS, shift)
     D = api.Docs.from_csr(tree, db_h)
     Q = api.Docs.from_csr(tree, q_h)
+    # launch configuration picked by the library's autotuner on a 50-query sample
+    Qs = api.Docs.from_csr(tree, q_h.subset(np.arange(min(50, q_h.n))))
+    tuned = api.flowtree_autotune(tree, tree.points, Qs, D)
+    del Qs
     nq, nd = Q.n_docs, D.n_docs
     n_pairs = nq * nd
     vocab = tree.points
@@ -332,7 +357,8 @@ def main():
         "vs_baseline": None, "dtype": "u32/f32", "data": "synthetic",
         "config": {"workload": WORKLOAD + (" [quick]" if args.quick else ""), "pairs_per_step_per_gpu": n_pairs,
                    "l2": "flushed (512 MiB write) before every timed step", "parallelism": "weak, %d shard(s)" % world,
-                   "launch_config": list(tree.get_config())},
+                   "launch_config": {"warps_per_cta": tuned[0], "stage_items": tuned[1],
+                                     "algo": ["auto", "warp", "thread"][tuned[2]], "picked_by": "ft_flowtree_autotune"}},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": statistics.mean(e2e_ms)},
         "gpu_launches": 3 * args.steps,

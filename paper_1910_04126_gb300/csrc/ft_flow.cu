@@ -476,7 +476,7 @@ extern "C" ft_status ft_flowtree_autotune(ft_tree* t, const float* vocab_dev, co
     const int maxn = round32(std::max(a->max_support + b->max_support, 32));
     std::vector<ft_flowtree_config> cands;
     const int caps[] = {maxn, 256, 384, 512, 768, 1024};
-    const int warps[] = {2, 4, 8};
+    const int warps[] = {2, 4, 6, 8};
     for (int cap : caps) {
         if (cap > maxn || cap > kMaxStage) continue;
         for (int w : warps) cands.push_back({w, cap, FT_ALGO_WARP});
