@@ -358,7 +358,8 @@ def main():
         "config": {"workload": WORKLOAD + (" [quick]" if args.quick else ""), "pairs_per_step_per_gpu": n_pairs,
                    "l2": "flushed (512 MiB write) before every timed step", "parallelism": "weak, %d shard(s)" % world,
                    "launch_config": {"warps_per_cta": tuned[0], "stage_items": tuned[1],
-                                     "algo": ["auto", "warp", "thread"][tuned[2]], "picked_by": "ft_flowtree_autotune"}},
+                                     "algo": ["auto", "warp", "thread"][tuned[2]], "stage_tables": tuned[3],
+                                     "picked_by": "ft_flowtree_autotune"}},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": statistics.mean(e2e_ms)},
         "gpu_launches": 3 * args.steps,

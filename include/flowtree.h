@@ -214,6 +214,10 @@ ft_status ft_flowtree_plain(const ft_tree* t, const float* vocab_dev, const ft_d
  *                   (the faster of the two on every measured workload).
  *   warps_per_cta : warps per CTA (1..8).
  *   stage_items   : merged support items each warp stages on chip (WARP).
+ *   stage_tables  : 1 = copy the vocabulary and the LCA table into shared
+ *                   memory per CTA when they fit (at most 32 KiB); 0 = read
+ *                   them through L1 (the default: one cached copy per SM
+ *                   leaves more shared memory for resident warps).
  * ft_flowtree_autotune times a few configurations on the given pairs (with
  * CUDA events on `stream`) and installs the fastest for this tree. */
 #define FT_ALGO_AUTO 0
@@ -223,6 +227,7 @@ typedef struct {
     int32_t warps_per_cta;
     int32_t stage_items;
     int32_t algo;
+    int32_t stage_tables;
 } ft_flowtree_config;
 ft_status ft_flowtree_set_config(ft_tree* t, const ft_flowtree_config* cfg);
 ft_status ft_flowtree_get_config(const ft_tree* t, ft_flowtree_config* cfg);

@@ -35,7 +35,8 @@ ALGO_AUTO, ALGO_WARP, ALGO_THREAD = 0, 1, 2
 
 
 class FlowtreeConfig(C.Structure):
-    _fields_ = [("warps_per_cta", C.c_int32), ("stage_items", C.c_int32), ("algo", C.c_int32)]
+    _fields_ = [("warps_per_cta", C.c_int32), ("stage_items", C.c_int32), ("algo", C.c_int32),
+                ("stage_tables", C.c_int32)]
 
 
 vp = C.c_void_p

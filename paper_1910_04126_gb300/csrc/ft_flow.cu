@@ -237,7 +237,7 @@ ft_status make_plan(const ft_tree* t, const ft_docs* a, const ft_docs* b, int64_
     if (p->algo == FT_ALGO_THREAD) {
         if (!thread_ok) return FT_EUNSUPPORTED;
         p->tmax = maxn <= 256 ? 256 : maxn <= 512 ? 512 : maxn <= 1024 ? 1024 : 2048;
-        p->tables_bytes = staged_tables_bytes(t);
+        p->tables_bytes = cfg.stage_tables ? staged_tables_bytes(t) : 0;
         p->smem = size_t(p->tables_bytes);
         int sms = 0, bps = 0;
         FT_TRY(ft_device_sms(&sms));
@@ -249,7 +249,7 @@ ft_status make_plan(const ft_tree* t, const ft_docs* a, const ft_docs* b, int64_
     int cap = cfg.stage_items > 0 ? round32(cfg.stage_items) : std::min(maxn, 512);
     cap = std::min(cap, kMaxStage);
     p->cap = cap;
-    p->tables_bytes = staged_tables_bytes(t);
+    p->tables_bytes = cfg.stage_tables ? staged_tables_bytes(t) : 0;
     p->smem = size_t(p->tables_bytes) + size_t(p->warps) * warpbuf_bytes(cap);
     int dev = 0, max_smem = 0, sms = 0;
     FT_CUDA(cudaGetDevice(&dev));
@@ -476,14 +476,15 @@ extern "C" ft_status ft_flowtree_autotune(ft_tree* t, const float* vocab_dev, co
     const int maxn = round32(std::max(a->max_support + b->max_support, 32));
     std::vector<ft_flowtree_config> cands;
     const int caps[] = {maxn, 256, 384, 512, 768, 1024};
-    const int warps[] = {2, 4, 6, 8};
+    const int warps[] = {3, 4, 5, 6, 7, 8};
     for (int cap : caps) {
         if (cap > maxn || cap > kMaxStage) continue;
-        for (int w : warps) cands.push_back({w, cap, FT_ALGO_WARP});
+        for (int w : warps)
+            for (int st : {0, 1}) cands.push_back({w, cap, FT_ALGO_WARP, st});
     }
     if (t->dim <= 8 && maxn <= kThreadMaxItems)
-        for (int w : {2, 4, 8}) cands.push_back({w, 0, FT_ALGO_THREAD});
-    if (cands.empty()) cands.push_back({kDefaultWarps, std::min(maxn, 512), FT_ALGO_WARP});
+        for (int w : {2, 4, 8}) cands.push_back({w, 0, FT_ALGO_THREAD, 1});
+    if (cands.empty()) cands.push_back({kDefaultWarps, std::min(maxn, 512), FT_ALGO_WARP, 0});
     cudaEvent_t e0, e1;
     FT_CUDA(cudaEventCreate(&e0));
     FT_CUDA(cudaEventCreate(&e1));

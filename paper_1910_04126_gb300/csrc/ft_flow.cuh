@@ -279,21 +279,49 @@ __device__ float flowtree_pair(const FlowCtx& c, const WarpBuf& w, const Tables&
     }
     __syncwarp();
 
-    // 2. LCA depth between neighbours; the set of depths that occur
-    uint32_t levelmask = 0;
-    for (int i = lane; i < n - 1; i += 32) {
-        const uint32_t r1 = w.rank[i], r2 = w.rank[i + 1];
-        const int dd = (r1 == r2) ? L + 1 : lca_ranks(tb, c.n_points, r1, r2);
-        w.D[i] = uint8_t(dd);
-        levelmask |= 1u << dd;
-    }
-    levelmask = __reduce_or_sync(FULL_MASK, levelmask);
-    __syncwarp();
-
     CompSum acc;
     int n_saved = 0;
     const int64_t slot0 = SAVE ? c.slot_ptr[pair] : 0;
-    int nl = n;  // live items
+
+    // 2. LCA depth between neighbours; the set of depths that occur.  A point
+    //    carried by both supports is a run of its own at the point level
+    //    (depth L+1): its mu and nu items sit side by side and are matched
+    //    here directly (distance 0), so the point level needs no pass.
+    uint32_t levelmask = 0;
+    for (int base = 0; base < n - 1; base += 32) {
+        const int i = base + int(lane);
+        const bool valid = i < n - 1;
+        bool same = false;
+        uint32_t f = 0;
+        if (valid) {
+            const uint32_t r1 = w.rank[i], r2 = w.rank[i + 1];
+            same = r1 == r2;
+            const int dd = same ? L + 1 : lca_ranks(tb, c.n_points, r1, r2);
+            w.D[i] = uint8_t(dd);
+            if (!same) levelmask |= 1u << dd;
+            if (same) {  // i is the mu item, i + 1 the nu item of the same point
+                const uint32_t ra = w.res[i], rb = w.res[i + 1];
+                f = min(ra, rb);
+                w.res[i] = ra - f;
+                w.res[i + 1] = rb - f;
+            }
+        }
+        if (SAVE) {
+            const unsigned emask = __ballot_sync(FULL_MASK, same);
+            if (same) {
+                const int64_t slot = slot0 + n_saved + __popc(emask & lmask_lt);
+                c.f_ia[slot] = unsigned(w.meta[i]) & 0x7FFFu;
+                c.f_ib[slot] = unsigned(w.meta[i + 1]) & 0x7FFFu;
+                c.f_f[slot] = f;
+                c.f_depth[slot] = uint8_t(L + 1);
+                c.f_dist[slot] = 0.0f;
+            }
+            n_saved += __popc(emask);
+        }
+    }
+    levelmask = __reduce_or_sync(FULL_MASK, levelmask);
+    __syncwarp();
+    int nl = n;  // items in the working set (exhausted ones are dropped after the first depth)
 
     // 3. bottom-up matching over the depths present, deepest first
     while (nl > 0 && levelmask != 0) {
@@ -345,8 +373,8 @@ __device__ float flowtree_pair(const FlowCtx& c, const WarpBuf& w, const Tables&
             bool emit = false;
             uint32_t f = 0;
             unsigned ia = 0, ib = 0;
-            if (valid) {
-                const uint32_t r = w.res[i];
+            const uint32_t r = valid ? w.res[i] : 0u;
+            if (r > 0) {
                 const unsigned mi = w.meta[i];
                 const unsigned side = mi >> 15;
                 const int nx = w.next[h];
@@ -427,8 +455,12 @@ __device__ float flowtree_pair(const FlowCtx& c, const WarpBuf& w, const Tables&
         }
         __syncwarp();
 
-        // pass C: drop exhausted items (stable, in place)
+        // pass C: drop exhausted items (stable, in place) and recompute the
+        // LCA depth between consecutive survivors (the minimum over the
+        // dropped span); only depths below k can remain
         int cnt = 0;
+        uint32_t nm = 0;
+        uint32_t carry_rank = 0;  // rank of the previous chunk's last survivor
         for (int base = 0; base < nl; base += 32) {
             const int i = base + int(lane);
             const bool valid = i < nl;
@@ -437,30 +469,43 @@ __device__ float flowtree_pair(const FlowCtx& c, const WarpBuf& w, const Tables&
             const uint16_t mt = valid ? w.meta[i] : uint16_t(0);
             const bool keep = r > 0;
             const unsigned km = __ballot_sync(FULL_MASK, keep);
+            // rank of the next survivor in this chunk (self if none)
+            const unsigned above = km & ~lmask_le;
+            const int nxt = above ? __ffs(above) - 1 : int(lane);
+            const uint32_t rk_next = __shfl_sync(FULL_MASK, rk, nxt);
+            const uint32_t rk_first = __shfl_sync(FULL_MASK, rk, km ? __ffs(km) - 1 : 0);
+            const uint32_t rk_last = __shfl_sync(FULL_MASK, rk, km ? 31 - __clz(km) : 0);
             __syncwarp();
+            const int o = cnt + __popc(km & lmask_lt);
             if (keep) {
-                const int o = cnt + __popc(km & lmask_lt);
                 w.rank[o] = rk;
                 w.res[o] = r;
                 w.meta[o] = mt;
+                if (above) {
+                    const int dd = (rk == rk_next) ? L + 1 : lca_ranks(tb, c.n_points, rk, rk_next);
+                    w.D[o] = uint8_t(dd);
+                    nm |= 1u << dd;
+                }
             }
+            if (lane == 0 && km && cnt > 0) {  // previous chunk's last survivor -> this chunk's first
+                const int dd = (carry_rank == rk_first) ? L + 1 : lca_ranks(tb, c.n_points, carry_rank, rk_first);
+                w.D[cnt - 1] = uint8_t(dd);
+                nm |= 1u << dd;
+            }
+            if (km) carry_rank = rk_last;
             cnt += __popc(km);
             __syncwarp();
         }
         nl = cnt;
-        // pass D: LCA depths between the survivors, remaining depths below k
-        uint32_t nm = 0;
-        for (int i = lane; i < nl - 1; i += 32) {
-            const uint32_t r1 = w.rank[i], r2 = w.rank[i + 1];
-            const int dd = (r1 == r2) ? L + 1 : lca_ranks(tb, c.n_points, r1, r2);
-            w.D[i] = uint8_t(dd);
-            nm |= 1u << dd;
-        }
         nm = __reduce_or_sync(FULL_MASK, nm);
         levelmask = nm & ((1u << k) - 1u);
         __syncwarp();
     }
-    if (nl > 0 && lane == 0) ft_flag(c.status, FT_DEV_EOVERFLOW);  // unmatched mass: cannot happen
+    if (nl > 0) {  // any mass left unmatched would be a bug: report it
+        bool left = false;
+        for (int i = lane; i < nl; i += 32) left |= w.res[i] > 0;
+        if (__any_sync(FULL_MASK, left) && lane == 0) ft_flag(c.status, FT_DEV_EOVERFLOW);
+    }
     if (SAVE && lane == 0) c.count[pair] = n_saved;
     float total = acc.value();
 #pragma unroll
