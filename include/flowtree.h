@@ -76,7 +76,8 @@ typedef struct ft_flows ft_flows; /* saved tree flows of a batch of pairs     */
 
 /* Limits of this build. */
 #define FT_MAX_LEVELS 14          /* L <= 14                                  */
-#define FT_MAX_SUPPORT 16384      /* distinct points per distribution          */
+#define FT_MAX_SUPPORT 16383      /* distinct points per distribution (a merged
+                                     pair's positions then fit 15 bits)        */
 #define FT_MASS_ONE 16777216      /* 2^24: total mass of every distribution   */
 
 /* Human-readable name of a status code (static string). */

@@ -326,9 +326,12 @@ __device__ float flowtree_pair(const FlowCtx& c, const WarpBuf& w, const Tables&
     // 3. bottom-up matching over the depths present, deepest first
     while (nl > 0 && levelmask != 0) {
         const int k = 31 - __clz(levelmask);
-        // pass A: per-side exclusive prefixes at every position, run heads
+        // pass A: per-side exclusive prefixes at every position; every run
+        // head links to the next one, with bit 15 set when the run holds
+        // residual on both sides (only such runs match anything)
         uint32_t gm = 0, gn = 0;
         int lasthead = -1;
+        bool any_mixed = false;
         for (int base = 0; base < nl; base += 32) {
             const int i = base + int(lane);
             const bool valid = i < nl;
@@ -338,15 +341,19 @@ __device__ float flowtree_pair(const FlowCtx& c, const WarpBuf& w, const Tables&
             const uint64_t v = side ? (uint64_t(r) << 32) : uint64_t(r);
             const uint64_t inc = warp_incl_scan_u64(v);
             const uint64_t ex = inc - v;
+            const uint32_t Gmi = gm + uint32_t(ex), Gni = gn + uint32_t(ex >> 32);
             if (valid) {
-                w.Gm[i] = gm + uint32_t(ex);
-                w.Gn[i] = gn + uint32_t(ex >> 32);
+                w.Gm[i] = Gmi;
+                w.Gn[i] = Gni;
             }
+            __syncwarp();
             const unsigned hb = __ballot_sync(FULL_MASK, head);
-            if (head) {
-                const unsigned before = hb & lmask_lt;
-                const int prev = before ? base + 31 - __clz(before) : lasthead;
-                if (prev >= 0) w.next[prev] = uint16_t(i);
+            const unsigned before = hb & lmask_lt;
+            const int prev = before ? base + 31 - __clz(before) : lasthead;
+            if (head && prev >= 0) {
+                const bool mixed = (Gmi - w.Gm[prev]) > 0 && (Gni - w.Gn[prev]) > 0;
+                any_mixed |= mixed;
+                w.next[prev] = uint16_t(i | (mixed ? 0x8000 : 0));
             }
             if (hb) lasthead = base + 31 - __clz(hb);
             const uint64_t tot = __shfl_sync(FULL_MASK, inc, 31);
@@ -356,9 +363,15 @@ __device__ float flowtree_pair(const FlowCtx& c, const WarpBuf& w, const Tables&
         if (lane == 0) {
             w.Gm[nl] = gm;
             w.Gn[nl] = gn;
-            w.next[lasthead] = uint16_t(nl);
+            const bool mixed = (gm - w.Gm[lasthead]) > 0 && (gn - w.Gn[lasthead]) > 0;
+            any_mixed |= mixed;
+            w.next[lasthead] = uint16_t(nl | (mixed ? 0x8000 : 0));
         }
         __syncwarp();
+        if (!__any_sync(FULL_MASK, any_mixed)) {  // every run one-sided: nothing to match at depth k
+            levelmask &= (1u << k) - 1u;
+            continue;
+        }
 
         // pass B: match inside every run, emit and price the pairs
         lasthead = -1;
@@ -374,10 +387,11 @@ __device__ float flowtree_pair(const FlowCtx& c, const WarpBuf& w, const Tables&
             uint32_t f = 0;
             unsigned ia = 0, ib = 0;
             const uint32_t r = valid ? w.res[i] : 0u;
-            if (r > 0) {
+            const unsigned link = valid ? unsigned(w.next[h]) : 0u;
+            if (r > 0 && (link & 0x8000u)) {  // live item in a run with both sides
                 const unsigned mi = w.meta[i];
                 const unsigned side = mi >> 15;
-                const int nx = w.next[h];
+                const int nx = int(link & 0x7FFFu);
                 const uint32_t Sm = w.Gm[h], Sn = w.Gn[h];
                 const uint32_t M = min(w.Gm[nx] - Sm, w.Gn[nx] - Sn);
                 const uint32_t* Go = side ? w.Gm : w.Gn;
