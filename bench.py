@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true", help="small workload (smoke of the bench itself)")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--skip-scale", action="store_true", help="omit the 1,000,000-document scale leg")
     ap.add_argument("--profile-case", nargs=2, type=int, metavar=("N_DB", "N_Q"),
                     help="only run the image-shaped batch N_Q x N_DB three times (a case for ncu); no timing")
     ap.add_argument("--config", default="0,0,0", help="warps_per_cta,stage_items,algo for --profile-case")
@@ -466,6 +467,12 @@ def extras(args, tree, D, Q, q_h, db_h, pts, shift, batched_value, dev, pk, pk_k
         "workload": "vocab %d x 300, %d docs (log-normal lengths, Zipf(1.1) words), %d queries, top-%d -> top-%d"
                     % (nwt, ndb, nqt, k1, TOPK)}
 
+    if not args.skip_scale:
+        try:
+            out["scale_knn_pipeline"] = scale_leg(args, dev)
+        except Exception as ex:  # report, do not lose the main line
+            out["scale_knn_pipeline"] = {"error": "%s: %s" % (type(ex).__name__, ex)}
+
     # CPU oracle on the host cores (bounded sample of the same image workload)
     cores = os.cpu_count() or 1
     r_n, n_n, dt_n = oracle_rate(pts, shift, db_h, q_h, 12.0 if not args.quick else 2.0, cores, seed=1)
@@ -475,6 +482,73 @@ def extras(args, tree, D, Q, q_h, db_h, pts, shift, batched_value, dev, pk, pk_k
                            "single_thread": {"value": r_1, "sample_pairs": n_1}}
     out["roofline_hbm"] = hbm_roofline(q_h, db_h, batched_value, pk, pk_kind)
     return out
+
+
+def scale_leg(args, dev):
+    """Scale configuration: 400,000 x 300 vocabulary, 1,000,000 documents, 256-query batches.
+
+    quadtree scan -> top-1,000 -> batched Flowtree -> top-10, captured once as a
+    CUDA graph and replayed; p50/p99 batch latency over the replays; recall@10
+    of the pipeline against exhaustive Flowtree (no prefilter) over all
+    documents for the first 100 queries.
+    """
+    import torch
+    from paper_1910_04126_gb300 import api, synth
+    n_words, n_db, nq, k1, k = (400000, 1000000, 256, 1000, TOPK) if not args.quick else (20000, 20000, 64, 200, TOPK)
+    t0 = time.time()
+    vocab = synth.mixture_vocab(n_words, 300, 1000, 0.3, 500)
+    db = synth.zipf_docs_bulk(n_words, n_db, 502, device=str(dev))
+    q = synth.zipf_docs_bulk(n_words, nq, 503, device=str(dev))
+    gen_s = time.time() - t0
+    t0 = time.time()
+    tree = api.Tree(torch.as_tensor(vocab, device=dev), LEVELS, synth.random_shift(300, 501))
+    D, Q = api.Docs.from_csr(tree, db), api.Docs.from_csr(tree, q)
+    torch.cuda.synchronize()
+    prep_s = time.time() - t0
+    # launch configuration for these documents, tuned on a 2-query cross product
+    Qs = api.Docs.from_csr(tree, q.subset(np.arange(2)))
+    tuned = api.flowtree_autotune(tree, tree.points, Qs, D)
+    del Qs
+    ws = torch.empty(api.knn_workspace_size(tree, D, Q, k1, k), dtype=torch.uint8, device=dev)
+    ids = torch.empty((nq, k), dtype=torch.int32, device=dev)
+    dist = torch.empty((nq, k), dtype=torch.float32, device=dev)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        for _ in range(2):
+            api.knn(tree, tree.points, D, Q, k1, k, workspace=ws, ids=ids, dist=dist, stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        api.knn(tree, tree.points, D, Q, k1, k, workspace=ws, ids=ids, dist=dist)
+    g.replay()
+    torch.cuda.synchronize()
+    lat = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(20):
+        e0.record()
+        g.replay()
+        e1.record()
+        e1.synchronize()
+        lat.append(e0.elapsed_time(e1))
+    lat.sort()
+    p50, p99 = lat[len(lat) // 2], lat[min(len(lat) - 1, int(0.99 * len(lat)))]
+    # exhaustive Flowtree for the first queries: the recall reference
+    n_ex = min(100, nq)
+    Qx = api.Docs.from_csr(tree, q.subset(np.arange(n_ex)))
+    costs = api.flowtree_batch(tree, tree.points, Qx, D)
+    ex_ids, _ = api.topk_f32(costs.view(n_ex, n_db), k)
+    del costs
+    got, ref = ids[:n_ex].cpu().numpy(), ex_ids.cpu().numpy()
+    recall = float(np.mean([len(set(got[i]) & set(ref[i])) / k for i in range(n_ex)]))
+    return {"flowtree_pairs_per_s": nq * k1 / (p50 * 1e-3), "scan_pairs_per_s": nq * n_db / (p50 * 1e-3),
+            "batch_ms_p50": p50, "batch_ms_p99": p99, "replays": len(lat), "graph": True,
+            "recall_at_10_vs_exhaustive_flowtree": recall, "recall_queries": n_ex,
+            "generate_s": gen_s, "tree_and_embed_s": prep_s, "launch_config": list(tuned),
+            "db_items": int(D.info.n_items), "db_embed_entries": int(D.info.n_embed),
+            "workload": "vocab %d x 300, %d docs (log-normal median 150, 10-2,000 words, Zipf(1.05)), "
+                        "%d-query batch, top-%d -> top-%d" % (n_words, n_db, nq, k1, k)}
 
 
 def hbm_roofline(q_h, db_h, pairs_per_s, pk, pk_kind):

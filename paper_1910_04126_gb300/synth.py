@@ -199,6 +199,63 @@ def zipf_docs(n_words: int, n_docs: int, seed: int, exponent: float = 1.1, media
     return csr_from_lists(words)
 
 
+def zipf_docs_bulk(n_words: int, n_docs: int, seed: int, exponent: float = 1.05, median: float = 150.0,
+                   log_sigma: float = 0.8, s_lo: int = 10, s_hi: int = 2000, device: str = "cpu",
+                   chunk: int = 100000) -> Docs:
+    """Vectorised variant of zipf_docs for millions of documents (torch, any device).
+
+    Per document: s = clip(round(LogNormal(ln median, log_sigma)), s_lo, s_hi)
+    target distinct words; 2 s + 64 Zipf draws are made, duplicates removed,
+    and the distinct words kept in random order up to s.  A document whose
+    draws hold fewer than s distinct words keeps all of them (documents near
+    s_hi come out slightly shorter).
+    """
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    p = torch.arange(1, n_words + 1, dtype=torch.float64, device=device).pow(-exponent)
+    cdf = torch.cumsum(p, 0)
+    cdf /= cdf[-1].clone()
+    lens = torch.exp(torch.randn(n_docs, generator=g, device=device, dtype=torch.float64) * log_sigma
+                     + np.log(median)).round().clamp(s_lo, min(s_hi, n_words)).to(torch.int64)
+    words_out, lens_out = [], []
+    for lo in range(0, n_docs, chunk):
+        hi = min(n_docs, lo + chunk)
+        s = lens[lo:hi]
+        m = 2 * s + 64
+        doc = torch.repeat_interleave(torch.arange(hi - lo, device=device), m)
+        u = torch.rand(doc.numel(), generator=g, device=device, dtype=torch.float64)
+        w = torch.searchsorted(cdf, u, right=True).clamp(max=n_words - 1)
+        key = torch.unique(doc * n_words + w)                     # distinct (doc, word), sorted
+        kdoc = key // n_words
+        pri = torch.rand(key.numel(), generator=g, device=device)
+        order = torch.argsort(kdoc.to(torch.float64) * 2.0 + pri.to(torch.float64))  # by doc, random within
+        key, kdoc = key[order], kdoc[order]
+        start = torch.zeros(hi - lo + 1, dtype=torch.int64, device=device)
+        start[1:] = torch.cumsum(torch.bincount(kdoc, minlength=hi - lo), 0)
+        pos = torch.arange(key.numel(), device=device) - start[kdoc]
+        keep = pos < s[kdoc]
+        key, kdoc = key[keep], kdoc[keep]
+        words_out.append((key % n_words).to(torch.int32).cpu().numpy())
+        lens_out.append(torch.bincount(kdoc, minlength=hi - lo).cpu().numpy())
+    ln = np.concatenate(lens_out).astype(np.int64)
+    rp = np.zeros(n_docs + 1, np.int64)
+    np.cumsum(ln, out=rp[1:])
+    w = np.concatenate(words_out)
+    return Docs(rp, w, np.ones(len(w), np.float32))
+
+
+def scale(n_words: int = 400000, dim: int = 300, n_db: int = 1000000, n_queries: int = 256,
+          levels: int = 12, device: str = "cpu") -> Workload:
+    """The scale configuration: 400,000 x 300 vocabulary, 1,000,000 documents (log-normal
+    lengths, median 150, 10..2,000 words, Zipf(1.05)), one 256-query batch."""
+    vocab = mixture_vocab(n_words, dim, 1000, 0.3, 500)
+    return Workload(vocab, random_shift(dim, 501), levels,
+                    zipf_docs_bulk(n_words, n_db, 502, device=device),
+                    zipf_docs_bulk(n_words, n_queries, 503, device=device))
+
+
 def text(n_words: int = 100000, dim: int = 300, n_db: int = 100000, n_queries: int = 1000,
          levels: int = 12) -> Workload:
     vocab = mixture_vocab(n_words, dim, 1000, 0.3, 300)
