@@ -314,7 +314,78 @@ void free_docs(ft_docs* d) {
     cudaFree(d->d_eptr);
     cudaFree(d->d_ekey);
     cudaFree(d->d_emass);
+    cudaFree(d->d_ukey);
+    cudaFree(d->d_uoff);
+    cudaFree(d->d_post);
     delete d;
+}
+
+// ---------------------------------------------------------------------------
+// inverted index of the embeddings (node key -> documents), for the scan
+// ---------------------------------------------------------------------------
+__global__ void k_entry_doc(const int64_t* __restrict__ eptr, int64_t n_docs, uint32_t* __restrict__ edoc) {
+    const int64_t warps = int64_t(gridDim.x) * (blockDim.x / 32);
+    for (int64_t doc = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) / 32; doc < n_docs; doc += warps)
+        for (int64_t j = eptr[doc] + lane_id(); j < eptr[doc + 1]; j += 32) edoc[j] = uint32_t(doc);
+}
+
+// postings in key order (documents ascending within a key: the sort is
+// stable and entries are laid out document by document); flag[i] = 1 where
+// a new key starts
+__global__ void k_postings(const uint32_t* __restrict__ perm, const uint32_t* __restrict__ ekey,
+                           const uint32_t* __restrict__ emass, const uint32_t* __restrict__ edoc, int64_t n,
+                           uint32_t* __restrict__ skey, uint2* __restrict__ post, int64_t* __restrict__ flag) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+        const uint32_t e = perm[i];
+        const uint32_t k = ekey[e];
+        skey[i] = k;
+        post[i] = make_uint2(edoc[e], emass[e]);
+        flag[i] = (i == 0 || ekey[perm[i - 1]] != k) ? 1 : 0;
+    }
+}
+
+__global__ void k_unique_keys(const uint32_t* __restrict__ skey, const int64_t* __restrict__ excl, int64_t n,
+                              uint32_t* __restrict__ ukey, uint32_t* __restrict__ uoff) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+        const bool start = (i == 0) || (skey[i] != skey[i - 1]);
+        if (start) {
+            const int64_t id = excl[i];
+            ukey[id] = skey[i];
+            uoff[id] = uint32_t(i);
+        }
+    }
+}
+
+ft_status build_index(ft_docs* d, cudaStream_t s) {
+    const int64_t n = d->n_embed;
+    if (n >= (int64_t(1) << 32)) return FT_EUNSUPPORTED;
+    TmpBufs tmp;
+    uint32_t *perm, *edoc, *skey;
+    int64_t *flag, *scan_tmp;
+    void* sort_tmp;
+    FT_TRY(tmp.get(&perm, size_t(n)));
+    FT_TRY(tmp.get(&edoc, size_t(n)));
+    FT_TRY(tmp.get(&skey, size_t(n)));
+    FT_TRY(tmp.get(&flag, size_t(n) + 1));
+    FT_TRY(tmp.get(&scan_tmp, ft_scan_tmp_elems(n + 1)));
+    FT_TRY(tmp.get(reinterpret_cast<char**>(&sort_tmp), ft_sort_tmp_bytes(n)));
+    FT_TRY(dmalloc(&d->d_post, size_t(n)));
+    k_entry_doc<<<grid_for(d->n_docs * 32, 256), 256, 0, s>>>(d->d_eptr, d->n_docs, edoc);
+    FT_TRY(ft_iota_u32(perm, n, s));
+    FT_TRY(ft_sort_perm_by_u32(d->d_ekey, perm, n, 32, sort_tmp, s));
+    k_postings<<<grid_for(n, 256), 256, 0, s>>>(perm, d->d_ekey, d->d_emass, edoc, n, skey, d->d_post, flag);
+    FT_CUDA(cudaMemsetAsync(flag + n, 0, 8, s));
+    FT_TRY(ft_exclusive_scan_i64(flag, flag, n + 1, scan_tmp, s));
+    FT_CUDA(cudaMemcpyAsync(&d->n_ukeys, flag + n, 8, cudaMemcpyDeviceToHost, s));
+    FT_CUDA(cudaStreamSynchronize(s));
+    FT_TRY(dmalloc(&d->d_ukey, size_t(d->n_ukeys)));
+    FT_TRY(dmalloc(&d->d_uoff, size_t(d->n_ukeys) + 1));
+    k_unique_keys<<<grid_for(n, 256), 256, 0, s>>>(skey, flag, n, d->d_ukey, d->d_uoff);
+    const uint32_t end = uint32_t(n);
+    FT_CUDA(cudaMemcpyAsync(d->d_uoff + d->n_ukeys, &end, 4, cudaMemcpyHostToDevice, s));
+    FT_CUDA(cudaGetLastError());
+    FT_CUDA(cudaStreamSynchronize(s));
+    return FT_OK;
 }
 
 ft_status read_status(const ft_tree* t, cudaStream_t s) {
@@ -412,6 +483,9 @@ ft_status embed(const ft_tree* t, const int64_t* row_ptr, const int32_t* word, c
     FT_CUDA(cudaStreamSynchronize(s));
     d->max_support = int(hmax[0]);
     d->max_embed = int(hmax[1]);
+    d->h_eptr.resize(size_t(n_docs) + 1);
+    FT_CUDA(cudaMemcpy(d->h_eptr.data(), d->d_eptr, size_t(n_docs + 1) * 8, cudaMemcpyDeviceToHost));
+    FT_TRY(build_index(d, s));
     return read_status(t, s);
 }
 

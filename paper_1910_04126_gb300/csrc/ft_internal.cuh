@@ -79,6 +79,13 @@ struct ft_docs {
     int64_t* d_eptr = nullptr;   // [n_docs+1] embedding offsets
     uint32_t* d_ekey = nullptr;  // [n_embed] node key
     uint32_t* d_emass = nullptr; // [n_embed] node mass
+    std::vector<int64_t> h_eptr; // host copy of d_eptr (launch planning without a device read)
+    // inverted index of the embedding: for every distinct node key, the
+    // documents holding it (ascending) and their masses
+    int64_t n_ukeys = 0;
+    uint32_t* d_ukey = nullptr;  // [n_ukeys] distinct keys, ascending
+    uint32_t* d_uoff = nullptr;  // [n_ukeys+1] posting ranges
+    uint2* d_post = nullptr;     // [n_embed] postings {document, mass}
 };
 
 struct ft_flows {

@@ -7,8 +7,10 @@
 //   S = sum_v w(v) min(mu_q(v), mu_j(v))   (over nodes both touch)
 //   C = 2^24 sum_{k=1..L+1} w_k = 2^24 (2^(L+1) - 1)
 // L1 = 2C - 2S exactly (int64, units of u * 2^-24).  S only needs the nodes
-// both distributions touch: query embeddings sit in shared-memory hash
-// tables, document embeddings are streamed past them.
+// both distributions touch, so the scan walks, for every node of the query,
+// the database's posting list of that node (the inverted index built with
+// the embedding): its cost is the number of (query node, document) matches,
+// not the product of the two embedding sizes.
 #include <algorithm>
 
 #include "ft_internal.cuh"
@@ -20,14 +22,18 @@ extern "C" ft_status ft_flowtree_batch(const ft_tree* t, const float* vocab_dev,
 
 namespace {
 
-constexpr uint32_t EMPTY = 0xFFFFFFFFu;
-constexpr int SCAN_THREADS = 256;
+#ifndef FT_SCAN_THREADS
+#define FT_SCAN_THREADS 512
+#endif
+#ifndef FT_SCAN_TILE
+#define FT_SCAN_TILE 4096  // largest shared-memory tile, documents
+#endif
+#ifndef FT_SCAN_UNROLL
+#define FT_SCAN_UNROLL 4   // warp loads of 32 postings in flight per step
+#endif
+constexpr int SCAN_THREADS = FT_SCAN_THREADS;
 constexpr int SEL_THREADS = 1024;
 constexpr int MAX_K1 = 4096;
-
-__device__ __forceinline__ uint32_t hslot(uint32_t key, int log2cap) {
-    return (key * 0x9E3779B1u) >> (32 - log2cap);
-}
 
 // edge weight carried by an embedding entry
 __device__ __forceinline__ int64_t entry_weight(uint32_t key, int L) {
@@ -44,84 +50,204 @@ struct ScanArgs {
     const uint32_t* q_ekey;
     const uint32_t* q_emass;
     int64_t nq;
-    const int64_t* d_eptr;
-    const uint32_t* d_ekey;
-    const uint32_t* d_emass;
+    const uint32_t* ukey;   // database index: distinct keys, ascending
+    const uint32_t* uoff;   // [n_ukeys+1] posting ranges
+    int64_t n_ukeys;
+    const uint2* post;      // postings {document, mass}, documents ascending within a key
     int64_t nd;
     int L;
-    int qb;         // queries per block
-    int log2cap;    // hash capacity per query
-    int docs_per_block;
-    uint64_t* keys;     // [nq][nd] (L1 << 24) | doc, or NULL
-    int64_t* l1_out;    // [nq][nd] or NULL
+    int tile;               // documents per shared-memory tile
+    int ecap;               // entry slots (>= the longest query embedding)
+    int64_t docs_per_range; // documents per block, a multiple of tile
+    uint64_t* keys;         // [nq][nd] (L1 << 24) | doc, or NULL
+    int64_t* l1_out;        // [nq][nd] or NULL
 };
 
-// grid: (query groups, document tiles)
-template <int QB>
-__global__ void __launch_bounds__(SCAN_THREADS) k_qt_scan(ScanArgs a) {
-    extern __shared__ __align__(16) uint32_t tab[];  // [QB][cap] keys then [QB][cap] masses
-    const int cap = 1 << a.log2cap;
-    uint32_t* tkey = tab;
-    uint32_t* tmass = tab + size_t(QB) * cap;
-    const int64_t q0 = int64_t(blockIdx.x) * QB;
-    const int nqb = int(min(int64_t(QB), a.nq - q0));
-    for (int i = threadIdx.x; i < QB * cap; i += blockDim.x) tkey[i] = EMPTY;
+// The tile keeps two 32-bit counters per document, S = lo + 2^16 hi: lo sums
+// the low 16 bits of each addend and hi the rest.  lo stays below 2^32 while a
+// document matches at most 65,536 query entries, hi below 2^24 because
+// S < 2^40.  (Two 32-bit shared-memory atomics measured faster than one
+// 64-bit one.)
+__device__ __forceinline__ void tile_add(uint32_t* S, int tile, uint32_t d, uint64_t v) {
+    atomicAdd(S + d, uint32_t(v & 0xFFFFu));
+    atomicAdd(S + tile + d, uint32_t(v >> 16));
+}
+
+__device__ __forceinline__ uint64_t tile_take(uint32_t* S, int tile, int d) {
+    const uint64_t v = uint64_t(S[d]) + (uint64_t(S[tile + d]) << 16);
+    S[d] = 0;
+    S[tile + d] = 0;
+    return v;
+}
+
+// Postings of [c, lim) with document < thi (documents ascend): galloping
+// then binary search, so an entry with n postings in the tile costs about
+// 2 log2(n) loads.
+__device__ __forceinline__ uint32_t count_below(const uint2* __restrict__ post, uint32_t c, uint32_t lim,
+                                                uint32_t thi) {
+    uint32_t lo = c, hi = lim, step = 1;
+    for (;;) {
+        const uint32_t probe = lo + step - 1;
+        if (probe >= lim) break;
+        if (__ldg(&post[probe].x) >= thi) {
+            hi = probe;
+            break;
+        }
+        lo = probe + 1;
+        step <<= 1;
+    }
+    while (lo < hi) {
+        const uint32_t mid = lo + ((hi - lo) >> 1);
+        if (__ldg(&post[mid].x) < thi) lo = mid + 1; else hi = mid;
+    }
+    return lo - c;
+}
+
+// exclusive scan of v[0..n) in place by the whole block; returns the total
+__device__ uint32_t block_exclusive_scan(uint32_t* v, int n, uint32_t* warp_tot) {
+    const int T = blockDim.x, per = (n + T - 1) / T;
+    const int b = min(n, int(threadIdx.x) * per), e = min(n, b + per);
+    uint32_t s = 0;
+    for (int i = b; i < e; ++i) s += v[i];
+    const uint32_t incl = warp_incl_scan_u32(s);
+    const int warp = int(threadIdx.x >> 5), nw = T >> 5;
+    if (lane_id() == 31) warp_tot[warp] = incl;
     __syncthreads();
-    for (int qi = 0; qi < nqb; ++qi) {
-        const int64_t b = a.q_eptr[q0 + qi], e = a.q_eptr[q0 + qi + 1];
-        for (int64_t j = b + threadIdx.x; j < e; j += blockDim.x) {
-            const uint32_t key = a.q_ekey[j];
-            uint32_t s = hslot(key, a.log2cap);
-            for (;;) {
-                const uint32_t old = atomicCAS(&tkey[qi * cap + s], EMPTY, key);
-                if (old == EMPTY) {
-                    tmass[qi * cap + s] = a.q_emass[j];
-                    break;
-                }
-                s = (s + 1) & uint32_t(cap - 1);
+    if (warp == 0) {
+        const uint32_t x = lane_id() < unsigned(nw) ? warp_tot[lane_id()] : 0u;
+        const uint32_t xi = warp_incl_scan_u32(x);
+        if (lane_id() < unsigned(nw)) warp_tot[lane_id()] = xi - x;
+        if (lane_id() == 31) warp_tot[32] = xi;
+    }
+    __syncthreads();
+    uint32_t run = warp_tot[warp] + incl - s;
+    for (int i = b; i < e; ++i) {
+        const uint32_t x = v[i];
+        v[i] = run;
+        run += x;
+    }
+    const uint32_t total = warp_tot[32];
+    __syncthreads();
+    return total;
+}
+
+// One block per (document range, query); block b covers range b / nq of
+// query b % nq, so blocks resident together read the same slice of the
+// long posting lists.  Every query entry keeps a cursor into its posting
+// list.  Per tile of documents [tlo, thi):
+//   1. each entry counts its postings in the tile (galloping search);
+//   2. a block scan lays those postings out as one flat range;
+//   3. the warps split the flat range evenly (a contiguous share each) and
+//      walk it entry by entry, FT_SCAN_UNROLL loads of 32 postings in flight
+//      per warp, adding w(v) * min(mu_q(v), mu_doc(v)) to the document's
+//      shared-memory counter;
+//   4. the tile is written out as L1 = 2C - 2S and the cursors advance.
+// The even split keeps the warps of a block busy alike however the work is
+// spread over the entries (one node shared by every document holds as many
+// postings per tile as all the rare words together).
+__global__ void __launch_bounds__(SCAN_THREADS) k_qt_scan(ScanArgs a) {
+    extern __shared__ __align__(16) uint32_t sm[];
+    __shared__ uint32_t warp_tot[33];
+    uint32_t* S = sm;  // [2][tile]
+    uint32_t* ecur = S + 2 * a.tile;
+    uint32_t* eend = ecur + a.ecap;
+    uint32_t* ew = eend + a.ecap;       // edge weight
+    uint32_t* emq = ew + a.ecap;        // query mass
+    uint32_t* pre = emq + a.ecap;       // [ecap+1] flat offsets of the tile's postings
+    const int64_t q = int64_t(blockIdx.x) % a.nq;
+    const int64_t d_lo = (int64_t(blockIdx.x) / a.nq) * a.docs_per_range;
+    const int64_t d_hi = min(a.nd, d_lo + a.docs_per_range);
+    if (d_lo >= d_hi) return;  // uniform over the block
+    const int64_t eb = a.q_eptr[q];
+    const int E = int(a.q_eptr[q + 1] - eb);
+    for (int e = threadIdx.x; e < E; e += blockDim.x) {
+        const uint32_t key = a.q_ekey[eb + e];
+        int64_t lo = 0, hi = a.n_ukeys;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (__ldg(a.ukey + mid) < key) lo = mid + 1; else hi = mid;
+        }
+        uint32_t c = 0, en = 0;
+        if (lo < a.n_ukeys && __ldg(a.ukey + lo) == key) {
+            c = __ldg(a.uoff + lo);
+            en = __ldg(a.uoff + lo + 1);
+            uint32_t h = en;  // first posting with doc >= d_lo
+            while (c < h) {
+                const uint32_t mid = c + ((h - c) >> 1);
+                if (int64_t(__ldg(&a.post[mid].x)) < d_lo) c = mid + 1; else h = mid;
             }
         }
+        ecur[e] = c;
+        eend[e] = en;
+        ew[e] = uint32_t(entry_weight(key, a.L));
+        emq[e] = a.q_emass[eb + e];
     }
+    for (int i = threadIdx.x; i < 2 * a.tile; i += blockDim.x) S[i] = 0;
     __syncthreads();
     const int64_t C2 = (int64_t(1) << 25) * ((int64_t(1) << (a.L + 1)) - 1);  // 2C
     const unsigned lane = lane_id();
     const int warp = int(threadIdx.x >> 5), nwarps = int(blockDim.x >> 5);
-    const int64_t d_begin = int64_t(blockIdx.y) * a.docs_per_block;
-    const int64_t d_end = min(a.nd, d_begin + int64_t(a.docs_per_block));
-    for (int64_t doc = d_begin + warp; doc < d_end; doc += nwarps) {
-        int64_t acc[QB];
+    constexpr int U = FT_SCAN_UNROLL;
+    for (int64_t t_lo = d_lo; t_lo < d_hi; t_lo += a.tile) {
+        const int64_t t_hi = min(d_hi, t_lo + a.tile);
+        const uint32_t tlo = uint32_t(t_lo), thi = uint32_t(t_hi), n_t = thi - tlo;
+        for (int e = threadIdx.x; e < E; e += blockDim.x) {
+            const uint32_t c = ecur[e], en = eend[e];
+            pre[e] = c < en ? count_below(a.post, c, min(en, c + n_t), thi) : 0u;
+        }
+        __syncthreads();
+        const uint32_t P = block_exclusive_scan(pre, E, warp_tot);
+        if (threadIdx.x == 0) pre[E] = P;
+        __syncthreads();
+        // each warp takes a contiguous share of the flat range (whole groups
+        // of 32) and walks it entry piece by entry piece
+        const uint32_t groups = (P + 31u) >> 5, per = (groups + uint32_t(nwarps) - 1u) / uint32_t(nwarps);
+        uint32_t f = min(P, uint32_t(warp) * per * 32u);
+        const uint32_t f_end = min(P, f + per * 32u);
+        int e = 0;
+        if (f < f_end) {
+            int hi = E;  // last entry with pre[e] <= f
+            while (e < hi) {
+                const int mid = (e + hi + 1) >> 1;
+                if (pre[mid] <= f) e = mid; else hi = mid - 1;
+            }
+        }
+        while (f < f_end) {
+            while (pre[e + 1] <= f) ++e;
+            const uint32_t seg_end = min(pre[e + 1], f_end);
+            const uint32_t base = ecur[e] - pre[e];  // posting index = base + flat index
+            const uint64_t w = ew[e];
+            const uint32_t mq = emq[e];
+            for (; f + 32u * U <= seg_end; f += 32u * U) {
+                uint2 p[U];
 #pragma unroll
-        for (int qi = 0; qi < QB; ++qi) acc[qi] = 0;
-        const int64_t b = a.d_eptr[doc], e = a.d_eptr[doc + 1];
-        for (int64_t j = b + lane; j < e; j += 32) {
-            const uint32_t key = __ldg(a.d_ekey + j);
-            const uint32_t m = __ldg(a.d_emass + j);
-            const int64_t w = entry_weight(key, a.L);
-            const uint32_t s0 = hslot(key, a.log2cap);
+                for (int u = 0; u < U; ++u) p[u] = __ldg(a.post + base + f + lane + 32u * u);
 #pragma unroll
-            for (int qi = 0; qi < QB; ++qi) {
-                uint32_t s = s0;
-                for (;;) {
-                    const uint32_t k2 = tkey[qi * cap + s];
-                    if (k2 == key) {
-                        acc[qi] += w * int64_t(min(m, tmass[qi * cap + s]));
-                        break;
-                    }
-                    if (k2 == EMPTY) break;
-                    s = (s + 1) & uint32_t(cap - 1);
+                for (int u = 0; u < U; ++u) tile_add(S, a.tile, p[u].x - tlo, w * min(mq, p[u].y));
+            }
+            if (f < seg_end) {
+                uint2 p[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const uint32_t g = f + lane + 32u * u;
+                    p[u] = g < seg_end ? __ldg(a.post + base + g) : make_uint2(0xFFFFFFFFu, 0u);
                 }
-            }
-        }
 #pragma unroll
-        for (int qi = 0; qi < QB; ++qi) {
-            const int64_t S = warp_sum_i64(acc[qi]);
-            if (lane == 0 && qi < nqb) {
-                const int64_t l1 = C2 - 2 * S;
-                const int64_t o = (q0 + qi) * a.nd + doc;
-                if (a.keys) a.keys[o] = (uint64_t(l1) << 24) | uint64_t(doc);
-                if (a.l1_out) a.l1_out[o] = l1;
+                for (int u = 0; u < U; ++u)
+                    if (p[u].x != 0xFFFFFFFFu) tile_add(S, a.tile, p[u].x - tlo, w * min(mq, p[u].y));
+                f = seg_end;
             }
         }
+        __syncthreads();
+        for (int i = threadIdx.x; i < int(n_t); i += blockDim.x) {
+            const int64_t doc = t_lo + i;
+            const int64_t l1 = C2 - 2 * int64_t(tile_take(S, a.tile, i));
+            const int64_t o = q * a.nd + doc;
+            if (a.keys) a.keys[o] = (uint64_t(l1) << 24) | uint64_t(doc);
+            if (a.l1_out) a.l1_out[o] = l1;
+        }
+        for (int e = threadIdx.x; e < E; e += blockDim.x) ecur[e] += pre[e + 1] - pre[e];
+        __syncthreads();
     }
 }
 
@@ -284,66 +410,67 @@ int grid_for(int64_t work, int threads) {
 }
 
 struct ScanPlan {
-    int qb = 16;
-    int log2cap = 6;
+    int tile = 4096;
+    int ecap = 1;
+    int64_t docs_per_range = 0;
+    int64_t blocks = 0;
     size_t smem = 0;
-    int docs_per_block = 256;
 };
 
-ft_status plan_scan(const ft_docs* queries, ScanPlan* p) {
-    int log2cap = 5;
-    while ((1 << log2cap) < 2 * std::max(queries->max_embed, 1)) ++log2cap;
-    p->log2cap = log2cap;
+ft_status plan_scan(const ft_tree* t, const ft_docs* q, const ft_docs* d, ScanPlan* p) {
     int dev = 0, max_smem = 0;
     FT_CUDA(cudaGetDevice(&dev));
     FT_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    const size_t per_q = size_t(8) << log2cap;
-    int qb = 16;
-    while (qb > 1 && per_q * qb > size_t(max_smem) / 2) qb >>= 1;
-    if (per_q * qb > size_t(max_smem)) return FT_EUNSUPPORTED;
-    p->qb = qb;
-    p->smem = per_q * qb;
-    return FT_OK;
-}
-
-template <int QB>
-ft_status launch_scan_q(const ScanPlan& p, ScanArgs a, cudaStream_t s) {
-    auto fn = &k_qt_scan<QB>;
+    p->ecap = std::max(q->max_embed, 1);
+    const size_t entry_bytes = size_t(20) * p->ecap + 4;
+    // the largest tile (<= 4096 documents) that leaves room for three blocks
+    // per SM, else for one
+    const size_t room = size_t(max_smem) - 1024;  // less the block's static shared memory
+    int tile = FT_SCAN_TILE;
+    while (tile > 256 && 3 * (size_t(8) * tile + entry_bytes) > room) tile >>= 1;
+    if (size_t(8) * tile + entry_bytes > room || p->ecap > 65536) return FT_EUNSUPPORTED;
+    p->tile = tile;
+    p->smem = size_t(8) * tile + entry_bytes;
     int bps = 0;
-    FT_TRY(ft_prepare_kernel(reinterpret_cast<const void*>(fn), SCAN_THREADS, p.smem, &bps));
+    FT_TRY(ft_prepare_kernel(reinterpret_cast<const void*>(&k_qt_scan), SCAN_THREADS, p->smem, &bps));
     if (bps < 1) return FT_EUNSUPPORTED;
-    dim3 grid(unsigned((a.nq + QB - 1) / QB), unsigned((a.nd + p.docs_per_block - 1) / p.docs_per_block));
-    fn<<<grid, SCAN_THREADS, p.smem, s>>>(a);
-    FT_CUDA(cudaGetLastError());
+    // split each query's documents into ranges until about four waves of
+    // blocks exist; a range spans whole tiles
+    const int64_t tiles = (d->n_docs + tile - 1) / tile;
+    const int64_t want = int64_t(4) * t->num_sms * bps;
+    int64_t ranges = std::min(tiles, std::max<int64_t>(1, (want + q->n_docs - 1) / q->n_docs));
+    const int64_t tiles_per_range = (tiles + ranges - 1) / ranges;
+    ranges = (tiles + tiles_per_range - 1) / tiles_per_range;
+    p->docs_per_range = tiles_per_range * tile;
+    p->blocks = ranges * q->n_docs;
+    if (p->blocks > 0x7FFFFFFF) return FT_EUNSUPPORTED;
     return FT_OK;
 }
 
 ft_status launch_scan(const ft_tree* t, const ft_docs* q, const ft_docs* d, uint64_t* keys, int64_t* l1,
                       cudaStream_t s) {
+    if (q->n_docs == 0) return FT_OK;
     ScanPlan p;
-    FT_TRY(plan_scan(q, &p));
+    FT_TRY(plan_scan(t, q, d, &p));
     ScanArgs a{};
     a.q_eptr = q->d_eptr;
     a.q_ekey = q->d_ekey;
     a.q_emass = q->d_emass;
     a.nq = q->n_docs;
-    a.d_eptr = d->d_eptr;
-    a.d_ekey = d->d_ekey;
-    a.d_emass = d->d_emass;
+    a.ukey = d->d_ukey;
+    a.uoff = d->d_uoff;
+    a.n_ukeys = d->n_ukeys;
+    a.post = d->d_post;
     a.nd = d->n_docs;
     a.L = t->levels;
-    a.qb = p.qb;
-    a.log2cap = p.log2cap;
-    a.docs_per_block = p.docs_per_block;
+    a.tile = p.tile;
+    a.ecap = p.ecap;
+    a.docs_per_range = p.docs_per_range;
     a.keys = keys;
     a.l1_out = l1;
-    switch (p.qb) {
-        case 16: return launch_scan_q<16>(p, a, s);
-        case 8: return launch_scan_q<8>(p, a, s);
-        case 4: return launch_scan_q<4>(p, a, s);
-        case 2: return launch_scan_q<2>(p, a, s);
-        default: return launch_scan_q<1>(p, a, s);
-    }
+    k_qt_scan<<<unsigned(p.blocks), SCAN_THREADS, p.smem, s>>>(a);
+    FT_CUDA(cudaGetLastError());
+    return FT_OK;
 }
 
 ft_status check_scan(const ft_tree* t, const ft_docs* q, const ft_docs* d, int32_t k1) {

@@ -70,7 +70,10 @@ ft_status ft_prepare_kernel(const void* fn, int threads, size_t smem, int* block
     if (!g_attr_set[{fn, dev}]) {
         int max_smem = 0;
         FT_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-        FT_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+        cudaFuncAttributes fa{};
+        FT_CUDA(cudaFuncGetAttributes(&fa, fn));  // static shared memory counts against the same limit
+        FT_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     max_smem - int(fa.sharedSizeBytes)));
         g_attr_set[{fn, dev}] = true;
     }
     int bps = 0;
