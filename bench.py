@@ -67,6 +67,9 @@ def parse():
     ap.add_argument("--profile-case", nargs=2, type=int, metavar=("N_DB", "N_Q"),
                     help="only run the image-shaped batch N_Q x N_DB three times (a case for ncu); no timing")
     ap.add_argument("--config", default="0,0,0", help="warps_per_cta,stage_items,algo for --profile-case")
+    ap.add_argument("--profile-scan", nargs=2, type=int, metavar=("N_DB", "N_Q"),
+                    help="only run the quadtree scan + top-1,000 of N_Q text-shaped queries over N_DB documents "
+                         "(vocabulary 100,000 x 300) three times (a case for ncu); no timing")
     return ap.parse_args()
 
 
@@ -83,6 +86,25 @@ def profile_case(args):
         api.flowtree_batch(tree, tree.points, Q, D, out=out)
     torch.cuda.synchronize()
     print("profile case done: %d pairs, config %s, status %d" % (n_db * n_q, args.config, tree.status()))
+
+
+def profile_scan(args):
+    import torch
+    from paper_1910_04126_gb300 import api, synth
+    n_db, n_q = args.profile_scan
+    vocab = synth.mixture_vocab(100000, 300, 1000, 0.3, 500)
+    db = synth.zipf_docs_bulk(100000, n_db, 502, device="cuda")
+    q = synth.zipf_docs_bulk(100000, n_q, 503, device="cuda")
+    tree = api.Tree(torch.as_tensor(vocab, device="cuda"), LEVELS, synth.random_shift(300, 501))
+    D, Q = api.Docs.from_csr(tree, db), api.Docs.from_csr(tree, q)
+    k1 = min(1000, n_db)
+    ws = torch.empty(api._ffi.load().ft_quadtree_scan_workspace_size(tree.handle, Q.handle, D.handle, k1),
+                     dtype=torch.uint8, device="cuda")
+    for _ in range(3):
+        api.quadtree_scan(tree, Q, D, k1, workspace=ws)
+    torch.cuda.synchronize()
+    print("profile scan done: %d x %d, %d db embedding entries, status %d"
+          % (n_q, n_db, D.info.n_embed, tree.status()))
 
 
 # ---------------------------------------------------------------------------
@@ -236,6 +258,9 @@ def main():
     if args.profile_case:
         profile_case(args)
         return
+    if args.profile_scan:
+        profile_scan(args)
+        return
 
     import torch
     import torch.distributed as dist
@@ -363,7 +388,9 @@ def main():
                                      "picked_by": "ft_flowtree_autotune"}},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": statistics.mean(e2e_ms)},
-        "gpu_launches": 3 * args.steps,
+        # per step: the Flowtree launch (plus the warp launch for overflow
+        # pairs when the lane-per-pair form runs), then keys + select
+        "gpu_launches": (4 if tuned[2] == 2 else 3) * args.steps,
         "clocks": clocks,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": alu_peak / 1e12, "unit": "Tops/s",
                      "frac": achieved / alu_peak, "traffic": traffic,
@@ -397,6 +424,7 @@ def extras(args, tree, D, Q, q_h, db_h, pts, shift, batched_value, dev, pk, pk_k
     plain = n_plain / (e0.elapsed_time(e1) * 1e-3)
     out["plain_per_pair"] = {"value": plain, "unit": UNIT, "sample_pairs": n_plain,
                              "batched_speedup": batched_value / plain}
+    out["match_depth_histogram"] = depth_histogram(tree, Q, D, pa, pb)
 
     # forward + backward (differentiation workload)
     nw, npairs = (30000, 4096) if not args.quick else (5000, 512)
@@ -464,12 +492,13 @@ def extras(args, tree, D, Q, q_h, db_h, pts, shift, batched_value, dev, pk, pk_k
     out["text_knn_pipeline"] = {
         "flowtree_pairs_per_s": nqt * k1 / (ms3 * 1e-3), "queries_per_s": nqt / (ms3 * 1e-3),
         "scan_pairs_per_s": nqt * ndb / (ms3 * 1e-3), "batch_ms_median": ms3, "graph": True,
+        "scan_roofline": scan_roofline(t3, Q3, D3, pk, pk_kind),
         "workload": "vocab %d x 300, %d docs (log-normal lengths, Zipf(1.1) words), %d queries, top-%d -> top-%d"
                     % (nwt, ndb, nqt, k1, TOPK)}
 
     if not args.skip_scale:
         try:
-            out["scale_knn_pipeline"] = scale_leg(args, dev)
+            out["scale_knn_pipeline"] = scale_leg(args, dev, pk, pk_kind)
         except Exception as ex:  # report, do not lose the main line
             out["scale_knn_pipeline"] = {"error": "%s: %s" % (type(ex).__name__, ex)}
 
@@ -484,7 +513,7 @@ def extras(args, tree, D, Q, q_h, db_h, pts, shift, batched_value, dev, pk, pk_k
     return out
 
 
-def scale_leg(args, dev):
+def scale_leg(args, dev, pk, pk_kind):
     """Scale configuration: 400,000 x 300 vocabulary, 1,000,000 documents, 256-query batches.
 
     quadtree scan -> top-1,000 -> batched Flowtree -> top-10, captured once as a
@@ -544,11 +573,59 @@ def scale_leg(args, dev):
     recall = float(np.mean([len(set(got[i]) & set(ref[i])) / k for i in range(n_ex)]))
     return {"flowtree_pairs_per_s": nq * k1 / (p50 * 1e-3), "scan_pairs_per_s": nq * n_db / (p50 * 1e-3),
             "batch_ms_p50": p50, "batch_ms_p99": p99, "replays": len(lat), "graph": True,
+            "scan_roofline": scan_roofline(tree, Q, D, pk, pk_kind),
             "recall_at_10_vs_exhaustive_flowtree": recall, "recall_queries": n_ex,
             "generate_s": gen_s, "tree_and_embed_s": prep_s, "launch_config": list(tuned),
             "db_items": int(D.info.n_items), "db_embed_entries": int(D.info.n_embed),
             "workload": "vocab %d x 300, %d docs (log-normal median 150, 10-2,000 words, Zipf(1.05)), "
                         "%d-query batch, top-%d -> top-%d" % (n_words, n_db, nq, k1, k)}
+
+
+def depth_histogram(tree, Q, D, pa, pb):
+    """Tree depth at which the flow's pairs are matched, over a sample of pairs:
+    share of the matched pairs and of the transported mass per depth (0 =
+    root, LEVELS + 1 = same point)."""
+    from paper_1910_04126_gb300 import api
+    flows = api.Flows(tree, Q, D, pa, pb)
+    api.flowtree_batch(tree, tree.points, Q, D, pa, pb, flows=flows)
+    ex = flows.export()
+    dep = np.concatenate([x[3] for x in ex]).astype(np.int64)
+    f = np.concatenate([x[2] for x in ex]).astype(np.float64)
+    cnt = np.bincount(dep, minlength=LEVELS + 2)
+    mass = np.bincount(dep, weights=f, minlength=LEVELS + 2)
+    return {"sample_pairs": int(len(pa)), "pairs_per_depth": (cnt / cnt.sum()).round(4).tolist(),
+            "mass_per_depth": (mass / mass.sum()).round(4).tolist(),
+            "matched_pairs_per_pair": float(cnt.sum()) / len(pa)}
+
+
+def scan_roofline(tree, Q, D, pk, pk_kind):
+    """HBM roofline of the quadtree scan kernel (dense-L1 form: the same kernel
+    as the pipeline's, writing int64 L1 instead of select keys): algorithmic
+    bytes = 8 per posting visited + 8 per (query, document) output."""
+    import torch
+    from paper_1910_04126_gb300 import api
+    matches = api.quadtree_scan_matches(tree, Q, D)
+    out = torch.empty((Q.n_docs, D.n_docs), dtype=torch.int64, device=tree.device)
+    lib = api._ffi.load()
+    st = torch.cuda.current_stream()
+    run = lambda: api.check(lib.ft_quadtree_l1_dense(tree.handle, Q.handle, D.handle, api._ptr(out),
+                                                     api._stream(st)), "ft_quadtree_l1_dense")
+    run()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ts = []
+    for _ in range(5):
+        e0.record(st)
+        run()
+        e1.record(st)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = statistics.median(ts)
+    nbytes = 8.0 * matches + 8.0 * Q.n_docs * D.n_docs
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    del out
+    return {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": gbs / pk["hbm_gbs"],
+            "peak_kind": pk_kind, "kernel": "k_qt_scan", "kernel_ms": ms, "postings_visited": matches,
+            "postings_per_pair": matches / (Q.n_docs * D.n_docs), "algorithmic_bytes": nbytes}
 
 
 def hbm_roofline(q_h, db_h, pairs_per_s, pk, pk_kind):

@@ -132,7 +132,9 @@ ft_status ft_tree_status(const ft_tree* t, void* stream);
  * m_i = floor(w_i / W * 2^24), the remaining units go one each to the
  * largest fractional parts (ties: smaller rank); items left at 0 are dropped.
  * Also builds each document's sparse quadtree embedding (Sec. 2, l1
- * embedding of tree W1) for ft_quadtree_scan.
+ * embedding of tree W1) and the set's inverted index over it (for every
+ * tree node, the documents whose embedding holds it, ascending, with their
+ * masses: 12 B per embedding entry) for ft_quadtree_scan.
  * Synchronous.  FT_EINVAL for malformed CSR or weights; FT_EUNSUPPORTED for
  * a document with more than FT_MAX_SUPPORT distinct points.
  * ------------------------------------------------------------------------ */
@@ -211,10 +213,13 @@ ft_status ft_flowtree_plain(const ft_tree* t, const float* vocab_dev, const ft_d
  *   algo          : FT_ALGO_AUTO, FT_ALGO_WARP (a warp per pair, level by
  *                   level over the merged supports staged in shared memory)
  *                   or FT_ALGO_THREAD (a thread per pair, one sweep with a
- *                   stack of open tree nodes; dim <= 8 only).  AUTO = WARP
- *                   (the faster of the two on every measured workload).
+ *                   stack of open tree nodes, its item buffer in shared
+ *                   memory; pairs that outgrow the buffer are finished by
+ *                   the warp form in a second launch; dim <= 8 only).
+ *                   AUTO = WARP; ft_flowtree_autotune picks either.
  *   warps_per_cta : warps per CTA (1..8).
- *   stage_items   : merged support items each warp stages on chip (WARP).
+ *   stage_items   : WARP: merged support items each warp stages on chip.
+ *                   THREAD: item buffer entries per thread (8 B each).
  *   stage_tables  : 1 = copy the vocabulary and the LCA table into shared
  *                   memory per CTA when they fit (at most 32 KiB); 0 = read
  *                   them through L1 (the default: one cached copy per SM
@@ -285,6 +290,14 @@ ft_status ft_quadtree_scan(const ft_tree* t, const ft_docs* queries, const ft_do
                            int64_t* cand_l1_out_dev, void* stream);
 ft_status ft_quadtree_l1_dense(const ft_tree* t, const ft_docs* queries, const ft_docs* db,
                                int64_t* l1_all_out_dev, void* stream);
+
+/* Work of the scan, for measurement: the number of (query node, database
+ * document) matches the scan visits, i.e. the sum over the queries and the
+ * nodes of their embeddings of the number of database documents holding
+ * that node.  Each visit reads one 8-byte posting.  Synchronous; writes the
+ * count to *matches_out_host. */
+ft_status ft_quadtree_scan_matches(const ft_tree* t, const ft_docs* queries, const ft_docs* db,
+                                   int64_t* matches_out_host);
 
 /* ------------------------------------------------------------------------
  * k-nearest-neighbour pipeline (Sec. 5.2): quadtree scan -> top-k1 ->

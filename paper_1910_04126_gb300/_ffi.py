@@ -71,6 +71,7 @@ SIGNATURES = {
     "ft_quadtree_scan_workspace_size": (sz, [vp, vp, vp, i32]),
     "ft_quadtree_scan": (i32, [vp, vp, vp, i32, vp, sz, vp, vp, vp]),
     "ft_quadtree_l1_dense": (i32, [vp, vp, vp, vp, vp]),
+    "ft_quadtree_scan_matches": (i32, [vp, vp, vp, C.POINTER(i64)]),
     "ft_knn_workspace_size": (sz, [vp, vp, vp, i32, i32]),
     "ft_knn": (i32, [vp, vp, vp, vp, i32, i32, vp, sz, vp, vp, vp]),
     "ft_topk_f32_workspace_size": (sz, [i64, i64]),

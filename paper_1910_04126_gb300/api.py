@@ -311,6 +311,14 @@ def quadtree_l1_dense(tree: Tree, queries: Docs, db: Docs, stream=None) -> torch
     return out
 
 
+def quadtree_scan_matches(tree: Tree, queries: Docs, db: Docs) -> int:
+    """(query node, database document) matches the scan visits (ft_quadtree_scan_matches)."""
+    n = C.c_int64(0)
+    check(_ffi.load().ft_quadtree_scan_matches(tree.handle, queries.handle, db.handle, C.byref(n)),
+          "ft_quadtree_scan_matches")
+    return int(n.value)
+
+
 def knn_workspace_size(tree: Tree, db: Docs, queries: Docs, k1: int, k: int) -> int:
     return int(_ffi.load().ft_knn_workspace_size(tree.handle, db.handle, queries.handle, k1, k))
 

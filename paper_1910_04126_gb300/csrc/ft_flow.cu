@@ -27,12 +27,13 @@ __global__ void __launch_bounds__(256) k_flowtree_persistent(FlowCtx c, int cap,
     const int64_t gw = int64_t(blockIdx.x) * (blockDim.x >> 5) + warp;
     WarpBuf gbuf = sbuf;
     if (c.gscratch) gbuf = carve_warpbuf(c.gscratch + size_t(gw) * c.gscratch_warp_bytes, c.gscratch_items);
+    const int64_t n_pairs = c.n_dev ? int64_t(*c.n_dev) : c.n_pairs;
     for (;;) {
         unsigned long long first = 0;
         if (lane == 0) first = atomicAdd(reinterpret_cast<unsigned long long*>(c.queue), (unsigned long long)grab);
         first = __shfl_sync(FULL_MASK, first, 0);
-        if (first >= (unsigned long long)c.n_pairs) break;
-        const int64_t last = min(int64_t(first) + grab, c.n_pairs);
+        if (first >= (unsigned long long)n_pairs) break;
+        const int64_t last = min(int64_t(first) + grab, n_pairs);
         for (int64_t q = int64_t(first); q < last; ++q) {
             const int64_t pair = c.order ? int64_t(c.order[q]) : q;
             int64_t da, db;
@@ -55,22 +56,27 @@ __global__ void __launch_bounds__(256) k_flowtree_persistent(FlowCtx c, int cap,
     }
 }
 
-// A thread per pair (low-dimensional ground sets).  The vocabulary and the
-// LCA table are copied to shared memory when they fit; each warp takes 32
-// consecutive pairs from the queue at a time.
-template <bool SAVE, int TMAX>
-__global__ void __launch_bounds__(256) k_flowtree_thread(FlowCtx c, int tables_bytes) {
+// A lane per pair (low-dimensional ground sets).  The vocabulary and the LCA
+// table are copied to shared memory when they fit; each warp takes 32
+// consecutive queue entries at a time, and every lane sweeps its own pair with
+// a `cap`-entry item buffer in shared memory (lane-interleaved).  A pair that
+// needs more is appended to ovf (count in *n_ovf) for the warp kernel.
+// Dynamic shared memory: [tables (if staged)] [warps][cap][32] uint64.
+template <bool SAVE>
+__global__ void __launch_bounds__(256) k_flowtree_thread(FlowCtx c, int cap, int tables_bytes, uint32_t* ovf,
+                                                         unsigned int* n_ovf) {
     extern __shared__ __align__(16) uint8_t smem[];
     const Tables tb = tables_bytes > 0 ? stage_tables(c, smem) : Tables{c.vocab, c.rmq};
-    uint64_t buf[TMAX];
     const unsigned lane = lane_id();
+    uint64_t* buf = reinterpret_cast<uint64_t*>(smem + tables_bytes) + size_t(threadIdx.x >> 5) * cap * 32 + lane;
     for (;;) {
+        __syncwarp();
         unsigned long long first = 0;
         if (lane == 0) first = atomicAdd(reinterpret_cast<unsigned long long*>(c.queue), 32ull);
         first = __shfl_sync(FULL_MASK, first, 0);
         if (first >= (unsigned long long)c.n_pairs) break;
         const int64_t q = int64_t(first) + lane;
-        if (q >= c.n_pairs) continue;
+        if (q >= c.n_pairs) continue;  // no warp-wide operation follows before the next __syncwarp
         const int64_t pair = c.order ? int64_t(c.order[q]) : q;
         int64_t da, db;
         if (c.pair_a) {
@@ -80,19 +86,18 @@ __global__ void __launch_bounds__(256) k_flowtree_thread(FlowCtx c, int tables_b
             da = pair / c.nb_cross;
             db = pair - da * c.nb_cross;
         }
-        float cost = __int_as_float(0x7fc00000);
         if (da < 0 || da >= c.na_docs || db < 0 || db >= c.nb_docs) {
             ft_flag(c.status, FT_DEV_EINVAL);
-        } else {
-            const int n = int(c.a_ptr[da + 1] - c.a_ptr[da]) + int(c.b_ptr[db + 1] - c.b_ptr[db]);
-            if (n > TMAX) {
-                ft_flag(c.status, FT_DEV_EOVERFLOW);
-            } else {
-                ThreadPair<SAVE, TMAX> tp(c, tb, buf);
-                cost = tp.run(pair, da, db);
-            }
+            c.cost_out[pair] = __int_as_float(0x7fc00000);
+            continue;
         }
-        c.cost_out[pair] = cost;
+        ThreadPair<SAVE> tp(c, tb, buf, cap);
+        const float cost = tp.run(pair, da, db);
+        if (tp.overflow) {
+            ovf[atomicAdd(n_ovf, 1u)] = uint32_t(pair);
+        } else {
+            c.cost_out[pair] = cost;
+        }
     }
 }
 
@@ -179,11 +184,17 @@ struct Plan {
     size_t gscratch_warp_bytes = 0;
     bool need_order = false;
     int64_t n_pairs = 0;
-    int tmax = 0;          // thread algorithm: item buffer per thread
     int tables_bytes = 0;  // vocabulary + LCA table staged in shared memory (0 = read from global)
+    // thread algorithm: the lane-per-pair launch; cap, warps, blocks, smem
+    // above then describe the warp-per-pair launch for its overflow pairs
+    int tcap = 0;          // item buffer entries per lane
+    int twarps = 0;
+    int tblocks = 0;
+    size_t tsmem = 0;
 };
 
 constexpr int kThreadMaxItems = 2048;
+constexpr int kThreadDefaultCap = 256;
 constexpr size_t kTablesMax = 32 * 1024;  // stage the tables when they are at most this big
 
 int staged_tables_bytes(const ft_tree* t) {
@@ -191,17 +202,10 @@ int staged_tables_bytes(const ft_tree* t) {
     return b <= kTablesMax ? int(b) : 0;
 }
 
-template <bool SAVE>
-void* thread_fn(int tmax) {
-    switch (tmax) {
-        case 256: return reinterpret_cast<void*>(&k_flowtree_thread<SAVE, 256>);
-        case 512: return reinterpret_cast<void*>(&k_flowtree_thread<SAVE, 512>);
-        case 1024: return reinterpret_cast<void*>(&k_flowtree_thread<SAVE, 1024>);
-        default: return reinterpret_cast<void*>(&k_flowtree_thread<SAVE, 2048>);
-    }
+void* thread_kernel(bool save) {
+    return save ? reinterpret_cast<void*>(&k_flowtree_thread<true>)
+                : reinterpret_cast<void*>(&k_flowtree_thread<false>);
 }
-
-void* thread_kernel(int tmax, bool save) { return save ? thread_fn<true>(tmax) : thread_fn<false>(tmax); }
 
 template <int MODE, bool SAVE>
 void* persistent_fn() {
@@ -234,27 +238,33 @@ ft_status make_plan(const ft_tree* t, const ft_docs* a, const ft_docs* b, int64_
     p->need_order = explicit_pairs && n_pairs > 1;
     const bool thread_ok = t->dim <= 8 && maxn <= kThreadMaxItems;
     p->algo = cfg.algo != FT_ALGO_AUTO ? cfg.algo : FT_ALGO_WARP;
-    if (p->algo == FT_ALGO_THREAD) {
-        if (!thread_ok) return FT_EUNSUPPORTED;
-        p->tmax = maxn <= 256 ? 256 : maxn <= 512 ? 512 : maxn <= 1024 ? 1024 : 2048;
-        p->tables_bytes = cfg.stage_tables ? staged_tables_bytes(t) : 0;
-        p->smem = size_t(p->tables_bytes);
-        int sms = 0, bps = 0;
-        FT_TRY(ft_device_sms(&sms));
-        FT_TRY(ft_prepare_kernel(thread_kernel(p->tmax, save), p->warps * 32, p->smem, &bps));
-        if (bps < 1) return FT_EUNSUPPORTED;
-        p->blocks = sms * bps;
-        return FT_OK;
-    }
-    int cap = cfg.stage_items > 0 ? round32(cfg.stage_items) : std::min(maxn, 512);
-    cap = std::min(cap, kMaxStage);
-    p->cap = cap;
-    p->tables_bytes = cfg.stage_tables ? staged_tables_bytes(t) : 0;
-    p->smem = size_t(p->tables_bytes) + size_t(p->warps) * warpbuf_bytes(cap);
     int dev = 0, max_smem = 0, sms = 0;
     FT_CUDA(cudaGetDevice(&dev));
     FT_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     FT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    p->tables_bytes = cfg.stage_tables ? staged_tables_bytes(t) : 0;
+    ft_flowtree_config wcfg = cfg;
+    if (p->algo == FT_ALGO_THREAD) {
+        if (!thread_ok) return FT_EUNSUPPORTED;
+        // lane per pair: stage_items = item buffer entries per lane
+        p->tcap = std::max(32, std::min(cfg.stage_items > 0 ? cfg.stage_items : kThreadDefaultCap, maxn));
+        // default: as many warps (up to 4) as the buffers leave room for
+        const int fit = int((size_t(max_smem) - size_t(p->tables_bytes)) / (size_t(p->tcap) * 32 * 8));
+        p->twarps = cfg.warps_per_cta > 0 ? cfg.warps_per_cta : std::max(1, std::min(kDefaultWarps, fit));
+        p->tsmem = size_t(p->tables_bytes) + size_t(p->twarps) * p->tcap * 32 * 8;
+        if (p->tsmem > size_t(max_smem)) return FT_EUNSUPPORTED;
+        int bps = 0;
+        FT_TRY(ft_prepare_kernel(thread_kernel(save), p->twarps * 32, p->tsmem, &bps));
+        if (bps < 1) return FT_EUNSUPPORTED;
+        p->tblocks = sms * bps;
+        // the warp launch for the overflow pairs: default shape
+        wcfg = {kDefaultWarps, 0, FT_ALGO_WARP, cfg.stage_tables};
+        p->warps = kDefaultWarps;
+    }
+    int cap = wcfg.stage_items > 0 ? round32(wcfg.stage_items) : std::min(maxn, 512);
+    cap = std::min(cap, kMaxStage);
+    p->cap = cap;
+    p->smem = size_t(p->tables_bytes) + size_t(p->warps) * warpbuf_bytes(cap);
     if (p->smem > size_t(max_smem)) return FT_EUNSUPPORTED;
     void* fn = persistent_kernel(mode, save);
     int bps = 0;
@@ -269,7 +279,8 @@ ft_status make_plan(const ft_tree* t, const ft_docs* a, const ft_docs* b, int64_
 }
 
 struct WsLayout {
-    unsigned int* queue;
+    unsigned int* queue;  // [0..1] queue, [2..3] overflow queue, [4] overflow count
+    uint32_t* ovf;        // thread algorithm: pairs left to the warp kernel
     uint32_t* order;
     uint32_t* keys;
     void* sort_tmp;
@@ -279,7 +290,8 @@ struct WsLayout {
 size_t layout(const Plan& p, void* base, WsLayout* out) {
     WsCarver w(base);
     WsLayout l{};
-    l.queue = w.take<unsigned int>(4);
+    l.queue = w.take<unsigned int>(8);
+    if (p.algo == FT_ALGO_THREAD) l.ovf = w.take<uint32_t>(size_t(p.n_pairs));
     if (p.need_order) {
         l.order = w.take<uint32_t>(size_t(p.n_pairs));
         l.keys = w.take<uint32_t>(size_t(p.n_pairs));
@@ -329,23 +341,33 @@ FlowCtx make_ctx(const ft_tree* t, const float* vocab, const ft_docs* a, const f
     return c;
 }
 
-ft_status launch_persistent(const Plan& p, FlowCtx c, bool save, cudaStream_t s) {
-    FT_CUDA(cudaMemsetAsync(c.queue, 0, 8, s));
-    if (p.algo == FT_ALGO_THREAD) {
-        void* fn = thread_kernel(p.tmax, save);
-        int tbytes = p.tables_bytes;
-        void* args[] = {&c, &tbytes};
-        FT_CUDA(cudaLaunchKernel(fn, dim3(p.blocks), dim3(p.warps * 32), args, p.smem, s));
-        return FT_OK;
-    }
+ft_status launch_warps(const Plan& p, const FlowCtx& c, bool save, cudaStream_t s) {
     const int64_t n_warps = int64_t(p.blocks) * p.warps;
-    int64_t grab = c.n_pairs / (n_warps * 32);
+    int64_t grab = c.n_dev ? 1 : c.n_pairs / (n_warps * 32);
     grab = std::max<int64_t>(1, std::min<int64_t>(grab, 16));
     void* fn = persistent_kernel(p.mode, save);
+    FlowCtx cc = c;
     int cap = p.cap, g = int(grab), tbytes = p.tables_bytes;
-    void* args[] = {&c, &cap, &g, &tbytes};
+    void* args[] = {&cc, &cap, &g, &tbytes};
     FT_CUDA(cudaLaunchKernel(fn, dim3(p.blocks), dim3(p.warps * 32), args, p.smem, s));
     return FT_OK;
+}
+
+ft_status launch_persistent(const Plan& p, const WsLayout& l, FlowCtx c, bool save, cudaStream_t s) {
+    FT_CUDA(cudaMemsetAsync(c.queue, 0, 32, s));
+    if (p.algo != FT_ALGO_THREAD) return launch_warps(p, c, save, s);
+    // lane per pair, then the warp kernel over the pairs it could not hold
+    void* fn = thread_kernel(save);
+    int tcap = p.tcap, tbytes = p.tables_bytes;
+    uint32_t* ovf = l.ovf;
+    unsigned int* n_ovf = c.queue + 4;
+    void* args[] = {&c, &tcap, &tbytes, &ovf, &n_ovf};
+    FT_CUDA(cudaLaunchKernel(fn, dim3(p.tblocks), dim3(p.twarps * 32), args, p.tsmem, s));
+    FlowCtx c2 = c;
+    c2.queue = c.queue + 2;
+    c2.order = l.ovf;
+    c2.n_dev = c.queue + 4;
+    return launch_warps(p, c2, save, s);
 }
 
 ft_status run_batch(const ft_tree* t, const float* vocab, const ft_docs* a, const ft_docs* b, const int32_t* pa,
@@ -382,7 +404,7 @@ ft_status run_batch(const ft_tree* t, const float* vocab, const ft_docs* a, cons
         c.f_depth = flows->d_depth;
         c.f_dist = flows->d_dist;
     }
-    return launch_persistent(p, c, save, s);
+    return launch_persistent(p, l, c, save, s);
 }
 
 template <class T>
@@ -423,7 +445,16 @@ extern "C" size_t ft_flowtree_batch_workspace_size(const ft_tree* t, const ft_do
     if (t->dim > 8 && make_plan(t, a, b, n_pairs, 1, false, true, t->cfg, &p1) != FT_OK) return 0;
     Plan p2 = p;
     if (t->dim > 8 && make_plan(t, a, b, n_pairs, 2, true, true, t->cfg, &p2) != FT_OK) return 0;
-    return std::max(layout(p, nullptr, nullptr), std::max(layout(p1, nullptr, nullptr), layout(p2, nullptr, nullptr)));
+    size_t need = std::max(layout(p, nullptr, nullptr), std::max(layout(p1, nullptr, nullptr), layout(p2, nullptr, nullptr)));
+    // room for the lane-per-pair form too, so that a workspace sized before
+    // ft_flowtree_autotune fits whatever it picks
+    Plan pt;
+    ft_flowtree_config tc = t->cfg;
+    tc.algo = FT_ALGO_THREAD;
+    tc.stage_items = 32;
+    if (t->dim <= 8 && make_plan(t, a, b, n_pairs, 0, false, true, tc, &pt) == FT_OK)
+        need = std::max(need, layout(pt, nullptr, nullptr));
+    return need;
 }
 
 extern "C" ft_status ft_flowtree_batch(const ft_tree* t, const float* vocab_dev, const ft_docs* a, const ft_docs* b,
@@ -482,8 +513,11 @@ extern "C" ft_status ft_flowtree_autotune(ft_tree* t, const float* vocab_dev, co
         for (int w : warps)
             for (int st : {0, 1}) cands.push_back({w, cap, FT_ALGO_WARP, st});
     }
-    if (t->dim <= 8 && maxn <= kThreadMaxItems)
-        for (int w : {2, 4, 8}) cands.push_back({w, 0, FT_ALGO_THREAD, 1});
+    if (t->dim <= 8 && maxn <= kThreadMaxItems) {
+        // lane per pair: warps per block x item buffer entries per lane
+        const int tc[][2] = {{3, 256}, {6, 128}};
+        for (const auto& x : tc) cands.push_back({x[0], x[1], FT_ALGO_THREAD, 0});
+    }
     if (cands.empty()) cands.push_back({kDefaultWarps, std::min(maxn, 512), FT_ALGO_WARP, 0});
     cudaEvent_t e0, e1;
     FT_CUDA(cudaEventCreate(&e0));

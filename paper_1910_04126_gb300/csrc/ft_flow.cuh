@@ -9,8 +9,11 @@
 //      side by side, mu first);
 //   2. D[i] = depth of the lowest common ancestor of merged items i, i+1
 //      (L+1 for the same point), from the range-minimum table over lcp;
-//   3. bottom-up matching, level-synchronously over the depths that occur
-//      among the D values, deepest first.  At depth k the depth-k nodes are
+//   3. bottom-up matching, level-synchronously, deepest first.  After the
+//      first depth, only the depths where a live mu item and a live nu item
+//      are adjacent (D of an adjacency whose sides differ) get a pass: below
+//      the deepest such depth every node holds one side only, so no other
+//      depth can match anything.  At depth k the depth-k nodes are
 //      the maximal runs with D >= k.  In every run the mu-residuals and the
 //      nu-residuals are matched in north-west-corner order: with per-side
 //      prefix sums, the unit at offset t of the run's mu stream meets the
@@ -21,7 +24,8 @@
 //      the two survivors), so each depth only touches live items.  The
 //      shallowest depth present clears everything (the totals are equal).
 //   4. every matched pair (x, y, f) is priced f * ||x - y|| (FP32 distance,
-//      compensated FP32 sum) and optionally saved.
+//      compensated FP32 sum) and optionally saved.  Pairs are queued and
+//      priced 32 at a time, so every lane has a pair to price.
 // Masses are 24-bit fixed point, so the flow itself is exact integer
 // arithmetic.
 #pragma once
@@ -56,6 +60,7 @@ struct FlowCtx {
     int64_t na_docs;
     int64_t nb_docs;
     const uint32_t* order;  // NULL -> identity
+    const unsigned int* n_dev;  // non-NULL: the pair count, read on the device (n_pairs is then a bound)
     unsigned int* queue;
     float* cost_out;
     // saved flows (NULL = not saved)
@@ -114,19 +119,22 @@ __device__ __forceinline__ float sqrt_approx(float x) {
     return r;
 }
 
-// Per-warp working set for `cap` merged items (cap multiple of 32), 21 B/item.
+// Per-warp working set for `cap` merged items (cap multiple of 32), 21 B/item
+// plus a 64-entry queue of matched pairs waiting to be priced.
 struct WarpBuf {
     uint32_t* rank;   // merged ranks (live items, compacted after every depth)
     uint32_t* res;    // residual mass
     uint32_t* Gm;     // [cap+32] exclusive mu-residual prefix at each position (+ total)
     uint32_t* Gn;     // [cap+32] exclusive nu-residual prefix
+    uint32_t* qe;     // [64] queued pairs: mu index | nu index << 16
+    uint32_t* qf;     // [64] their flow
     uint16_t* meta;   // bit 15 side (0 mu, 1 nu), bits 0..14 index in its support
     uint16_t* next;   // at run heads: position of the next run head
     uint8_t* D;       // LCA depth to the next item
 };
 
 __host__ __device__ inline size_t warpbuf_bytes(int cap) {
-    return size_t(cap) * (4 * 4 + 2 * 2 + 1) + 64 * 4 + 64;
+    return size_t(cap) * (4 * 4 + 2 * 2 + 1) + (64 + 128) * 4 + 64;
 }
 
 __device__ __forceinline__ WarpBuf carve_warpbuf(uint8_t* base, int cap) {
@@ -136,7 +144,9 @@ __device__ __forceinline__ WarpBuf carve_warpbuf(uint8_t* base, int cap) {
     w.res = p32 + cap;
     w.Gm = p32 + 2 * cap;
     w.Gn = p32 + 3 * cap + 32;
-    uint16_t* p16 = reinterpret_cast<uint16_t*>(p32 + 4 * cap + 64);
+    w.qe = p32 + 4 * cap + 64;
+    w.qf = w.qe + 64;
+    uint16_t* p16 = reinterpret_cast<uint16_t*>(p32 + 4 * cap + 64 + 128);
     w.meta = p16;
     w.next = p16 + cap;
     w.D = reinterpret_cast<uint8_t*>(p16 + 2 * cap);
@@ -210,6 +220,42 @@ __device__ __forceinline__ bool pair_docs(const FlowCtx& c, int64_t pair, int64_
         return false;
     }
     return true;
+}
+
+// Prices the first cnt (<= 32) queued pairs: acc += f * ||x_a - y_b||, and
+// with SAVE the distance goes to the pair's flow slot (queue entry j was
+// saved in slot qslot + j).
+template <int MODE, bool SAVE>
+__device__ __forceinline__ void price_queue(const FlowCtx& c, const WarpBuf& w, const Tables& tb, int64_t ao,
+                                            int64_t bo, int cnt, int64_t qslot, CompSum& acc) {
+    const unsigned lane = lane_id();
+    if (MODE == 0) {
+        if (int(lane) < cnt) {
+            const uint32_t e = w.qe[lane];
+            const uint32_t wa = __ldg(c.a_word + ao + (e & 0xFFFFu));
+            const uint32_t wb = __ldg(c.b_word + bo + (e >> 16));
+            const float dist = dist_lane(tb, c.dim, wa, wb);
+            acc.add(float(w.qf[lane]) * dist);
+            if (SAVE) c.f_dist[qslot + lane] = dist;
+        }
+    } else {
+        const unsigned grp = lane >> 3, sub = lane & 7u;
+        for (int r0 = 0; r0 < cnt; r0 += 4) {
+            const int e = r0 + int(grp);
+            uint32_t wa = 0, wb = 0;  // idle group: a zero-length pair (row 0 twice)
+            if (e < cnt) {
+                const uint32_t q = w.qe[e];
+                wa = __ldg(c.a_word + ao + (q & 0xFFFFu));
+                wb = __ldg(c.b_word + bo + (q >> 16));
+            }
+            // every lane takes part: dist_group shuffles across the warp
+            const float dist = dist_group<MODE>(c, wa, wb, sub);
+            if (e < cnt && sub == 0) {
+                acc.add(float(w.qf[e]) * dist);
+                if (SAVE) c.f_dist[qslot + e] = dist;
+            }
+        }
+    }
 }
 
 // Position of the n-th (0-based) set bit of mask; n < popc(mask).
@@ -298,6 +344,9 @@ __device__ float flowtree_pair(const FlowCtx& c, const WarpBuf& w, const Tables&
             same = r1 == r2;
             const int dd = same ? L + 1 : lca_ranks(tb, c.n_points, r1, r2);
             w.D[i] = uint8_t(dd);
+            // every depth present: items emptied at the point level may still
+            // separate a mu item from a nu item here, so the exact rule (a
+            // depth where the sides meet) waits for the first compaction
             if (!same) levelmask |= 1u << dd;
             if (same) {  // i is the mu item, i + 1 the nu item of the same point
                 const uint32_t ra = w.res[i], rb = w.res[i + 1];
@@ -321,6 +370,8 @@ __device__ float flowtree_pair(const FlowCtx& c, const WarpBuf& w, const Tables&
     }
     levelmask = __reduce_or_sync(FULL_MASK, levelmask);
     __syncwarp();
+    int qn = 0;                                   // pairs queued for pricing
+    int64_t qslot = SAVE ? slot0 + n_saved : 0;   // flow slot of queue entry 0
     int nl = n;  // items in the working set (exhausted ones are dropped after the first depth)
 
     // 3. bottom-up matching over the depths present, deepest first
@@ -368,14 +419,15 @@ __device__ float flowtree_pair(const FlowCtx& c, const WarpBuf& w, const Tables&
             w.next[lasthead] = uint16_t(nl | (mixed ? 0x8000 : 0));
         }
         __syncwarp();
-        if (!__any_sync(FULL_MASK, any_mixed)) {  // every run one-sided: nothing to match at depth k
-            levelmask &= (1u << k) - 1u;
-            continue;
-        }
+        // Every run one-sided (possible only before the first compaction,
+        // while the depths are all those present): nothing to match, but
+        // pass C still runs, to drop the items emptied at the point level and
+        // find the depths where the sides meet.
+        const int nl_b = __any_sync(FULL_MASK, any_mixed) ? nl : 0;
 
-        // pass B: match inside every run, emit and price the pairs
+        // pass B: match inside every run, queue and save the pairs
         lasthead = -1;
-        for (int base = 0; base < nl; base += 32) {
+        for (int base = 0; base < nl_b; base += 32) {
             const int i = base + int(lane);
             const bool valid = i < nl;
             const bool head = valid && (i == 0 || int(w.D[i - 1]) < k);
@@ -426,87 +478,105 @@ __device__ float flowtree_pair(const FlowCtx& c, const WarpBuf& w, const Tables&
             }
             const unsigned emask = __ballot_sync(FULL_MASK, emit);
             if (emask == 0) continue;
-            float dist = 0.0f;
-            if (k <= L) {
-                uint32_t wa = 0, wb = 0;
-                if (emit) {
-                    wa = __ldg(c.a_word + ao + ia);
-                    wb = __ldg(c.b_word + bo + ib);
-                }
-                if (MODE == 0) {
-                    if (emit) dist = dist_lane(tb, c.dim, wa, wb);
-                } else {
-                    const int nemit = __popc(emask);
-                    const unsigned grp = lane >> 3, sub = lane & 7u;
-                    const int my_e = __popc(emask & lmask_lt);
-                    for (int r0 = 0; r0 < nemit; r0 += 4) {
-                        const int e = r0 + int(grp);
-                        const int src = e < nemit ? nth_set_bit(emask, e) : 0;
-                        uint32_t ga = __shfl_sync(FULL_MASK, wa, src);
-                        uint32_t gb = __shfl_sync(FULL_MASK, wb, src);
-                        if (e >= nemit) ga = gb = 0;  // idle group: a zero-length pair (row 0 twice)
-                        // every lane takes part: dist_group shuffles across the warp
-                        const float dg = dist_group<MODE>(c, ga, gb, sub);
-                        const int from = ((my_e - r0) & 3) * 8;
-                        const float got = __shfl_sync(FULL_MASK, dg, from);
-                        if (emit && my_e >= r0 && my_e < r0 + 4) dist = got;
-                    }
-                }
+            // queue the pairs (k <= L: distinct points); they are priced 32
+            // at a time, one lane (MODE 0) or 8-lane group (MODE 1, 2) each
+            const int pos = __popc(emask & lmask_lt);
+            if (emit) {
+                w.qe[qn + pos] = ia | (ib << 16);
+                w.qf[qn + pos] = f;
             }
-            if (emit) acc.add(float(f) * dist);
             if (SAVE) {
-                const int o = n_saved + __popc(emask & lmask_lt);
                 if (emit) {
-                    const int64_t slot = slot0 + o;
+                    const int64_t slot = slot0 + n_saved + pos;
                     c.f_ia[slot] = ia;
                     c.f_ib[slot] = ib;
                     c.f_f[slot] = f;
                     c.f_depth[slot] = uint8_t(k);
-                    c.f_dist[slot] = dist;
                 }
                 n_saved += __popc(emask);
+            }
+            qn += __popc(emask);
+            if (qn >= 32) {
+                __syncwarp();
+                price_queue<MODE, SAVE>(c, w, tb, ao, bo, 32, qslot, acc);
+                __syncwarp();
+                const int rest = qn - 32;
+                uint32_t qe2 = 0, qf2 = 0;
+                if (int(lane) < rest) {
+                    qe2 = w.qe[32 + lane];
+                    qf2 = w.qf[32 + lane];
+                }
+                __syncwarp();
+                if (int(lane) < rest) {
+                    w.qe[lane] = qe2;
+                    w.qf[lane] = qf2;
+                }
+                __syncwarp();
+                qn = rest;
+                qslot += 32;
             }
         }
         __syncwarp();
 
         // pass C: drop exhausted items (stable, in place) and recompute the
         // LCA depth between consecutive survivors (the minimum over the
-        // dropped span); only depths below k can remain
+        // dropped span: a range-minimum lookup, unless the two were
+        // neighbours already); only depths below k can remain.  Ranks are
+        // below 2^24, so bit 31 carries the side.
         int cnt = 0;
         uint32_t nm = 0;
-        uint32_t carry_rank = 0;  // rank of the previous chunk's last survivor
+        uint32_t carry = 0;        // rank | side << 31 of the previous chunk's last survivor
+        bool carry_adj = false;    // ... which was that chunk's last item
+        unsigned carry_d = 0;      // ... and its D before this pass
         for (int base = 0; base < nl; base += 32) {
             const int i = base + int(lane);
             const bool valid = i < nl;
             const uint32_t r = valid ? w.res[i] : 0u;
             const uint32_t rk = valid ? w.rank[i] : 0u;
             const uint16_t mt = valid ? w.meta[i] : uint16_t(0);
+            const unsigned d_old = valid ? unsigned(w.D[i]) : 0u;
             const bool keep = r > 0;
             const unsigned km = __ballot_sync(FULL_MASK, keep);
-            // rank of the next survivor in this chunk (self if none)
+            const uint32_t rs = rk | ((unsigned(mt) >> 15) << 31);
+            // the next survivor in this chunk (self if none)
             const unsigned above = km & ~lmask_le;
             const int nxt = above ? __ffs(above) - 1 : int(lane);
-            const uint32_t rk_next = __shfl_sync(FULL_MASK, rk, nxt);
-            const uint32_t rk_first = __shfl_sync(FULL_MASK, rk, km ? __ffs(km) - 1 : 0);
-            const uint32_t rk_last = __shfl_sync(FULL_MASK, rk, km ? 31 - __clz(km) : 0);
+            const uint32_t rs_next = __shfl_sync(FULL_MASK, rs, nxt);
+            const uint32_t rs_first = __shfl_sync(FULL_MASK, rs, km ? __ffs(km) - 1 : 0);
+            const uint32_t rs_last = __shfl_sync(FULL_MASK, rs, km ? 31 - __clz(km) : 0);
+            const unsigned d31 = __shfl_sync(FULL_MASK, d_old, 31);
             __syncwarp();
             const int o = cnt + __popc(km & lmask_lt);
             if (keep) {
-                w.rank[o] = rk;
-                w.res[o] = r;
-                w.meta[o] = mt;
+                if (o != i) {
+                    w.rank[o] = rk;
+                    w.res[o] = r;
+                    w.meta[o] = mt;
+                }
                 if (above) {
-                    const int dd = (rk == rk_next) ? L + 1 : lca_ranks(tb, c.n_points, rk, rk_next);
-                    w.D[o] = uint8_t(dd);
-                    nm |= 1u << dd;
+                    int dd = int(d_old);
+                    if (nxt != int(lane) + 1) {
+                        const uint32_t rn = rs_next & 0x7FFFFFFFu;
+                        dd = (rk == rn) ? L + 1 : lca_ranks(tb, c.n_points, rk, rn);
+                    }
+                    if (o != i || dd != int(d_old)) w.D[o] = uint8_t(dd);
+                    if ((rs ^ rs_next) >> 31) nm |= 1u << dd;
                 }
             }
             if (lane == 0 && km && cnt > 0) {  // previous chunk's last survivor -> this chunk's first
-                const int dd = (carry_rank == rk_first) ? L + 1 : lca_ranks(tb, c.n_points, carry_rank, rk_first);
+                int dd;
+                if (carry_adj && (km & 1u)) {
+                    dd = int(carry_d);
+                } else {
+                    const uint32_t ra = carry & 0x7FFFFFFFu, rb = rs_first & 0x7FFFFFFFu;
+                    dd = (ra == rb) ? L + 1 : lca_ranks(tb, c.n_points, ra, rb);
+                }
                 w.D[cnt - 1] = uint8_t(dd);
-                nm |= 1u << dd;
+                if ((carry ^ rs_first) >> 31) nm |= 1u << dd;
             }
-            if (km) carry_rank = rk_last;
+            if (km) carry = rs_last;
+            carry_adj = (km >> 31) & 1u;
+            carry_d = d31;
             cnt += __popc(km);
             __syncwarp();
         }
@@ -514,6 +584,10 @@ __device__ float flowtree_pair(const FlowCtx& c, const WarpBuf& w, const Tables&
         nm = __reduce_or_sync(FULL_MASK, nm);
         levelmask = nm & ((1u << k) - 1u);
         __syncwarp();
+    }
+    if (qn > 0) {
+        __syncwarp();
+        price_queue<MODE, SAVE>(c, w, tb, ao, bo, qn, qslot, acc);
     }
     if (nl > 0) {  // any mass left unmatched would be a bug: report it
         bool left = false;

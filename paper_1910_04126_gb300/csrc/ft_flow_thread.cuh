@@ -21,7 +21,10 @@
 //
 // Work per pair: one pass over the s_mu + s_nu items plus one step per matched
 // pair, no warp-wide synchronisation.  Used for low-dimensional ground sets,
-// where pricing a pair is a few instructions.
+// where pricing a pair is a few instructions.  The item buffer lives in
+// shared memory, interleaved over the 32 lanes of the warp (entry e of a lane
+// at buf[32 e]); a pair whose buffer would outgrow `cap` entries stops and
+// reports overflow (the caller hands it to the warp-per-pair kernel).
 #pragma once
 
 #include "ft_flow.cuh"
@@ -44,11 +47,13 @@ __device__ __forceinline__ float tdist(const Tables& tb, int dim, uint32_t wa, u
     return dist_lane(tb, dim, wa, wb);
 }
 
-template <bool SAVE, int TMAX>
+template <bool SAVE>
 struct ThreadPair {
     const FlowCtx& c;
     const Tables& tb;
-    uint64_t* buf;
+    uint64_t* buf;  // this lane's entry 0; entry e at buf[32 e]
+    int cap;
+    bool overflow = false;
     uint8_t fgap[kThreadFrames];
     uint16_t fbeg[kThreadFrames];
     uint16_t fhead[kThreadFrames];
@@ -58,7 +63,10 @@ struct ThreadPair {
     int saved = 0;
     CompSum acc;
 
-    __device__ ThreadPair(const FlowCtx& c_, const Tables& tb_, uint64_t* buf_) : c(c_), tb(tb_), buf(buf_) {}
+    __device__ ThreadPair(const FlowCtx& c_, const Tables& tb_, uint64_t* buf_, int cap_)
+        : c(c_), tb(tb_), buf(buf_), cap(cap_) {}
+
+    __device__ __forceinline__ uint64_t& B(int e) { return buf[size_t(e) * 32]; }
 
     __device__ __forceinline__ void emit(uint64_t em, uint64_t en, uint32_t eta, int k) {
         uint32_t wa, wb;
@@ -91,10 +99,10 @@ struct ThreadPair {
         } else if (rh == e) {
             bend = rb;
         } else {
-            uint64_t el = buf[lh], er = buf[rh];
+            uint64_t el = B(lh), er = B(rh);
             if (tside(el) == tside(er)) {
                 if (rh != rb) {
-                    for (int t = rh; t < e; ++t) buf[rb + (t - rh)] = buf[t];
+                    for (int t = rh; t < e; ++t) B(rb + (t - rh)) = B(t);
                     bend = rb + (e - rh);
                 }
             } else {
@@ -105,12 +113,12 @@ struct ThreadPair {
                     const uint32_t eta = min(rl, rr);
                     if (tside(el) == 0) emit(el, er, eta, k); else emit(er, el, eta, k);
                     if (rl == eta) {
-                        if (++pl == rb) lx = true; else el = buf[pl];
+                        if (++pl == rb) lx = true; else el = B(pl);
                     } else {
                         el = tsetres(el, rl - eta);
                     }
                     if (rr == eta) {
-                        if (++pr == e) rx = true; else er = buf[pr];
+                        if (++pr == e) rx = true; else er = B(pr);
                     } else {
                         er = tsetres(er, rr - eta);
                     }
@@ -120,10 +128,10 @@ struct ThreadPair {
                     fhead[lf] = uint16_t(rb);
                     bend = rb;
                 } else if (lx) {
-                    buf[pr] = er;
+                    B(pr) = er;
                     fhead[lf] = uint16_t(pr);
                 } else {
-                    buf[pl] = el;
+                    B(pl) = el;
                     fhead[lf] = uint16_t(pl);
                     bend = rb;
                 }
@@ -132,7 +140,7 @@ struct ThreadPair {
         --nf;
     }
 
-    // returns the Flowtree value of the pair
+    // returns the Flowtree value of the pair (meaningless when overflow is set)
     __device__ float run(int64_t pair, int64_t da, int64_t db) {
         ao = c.a_ptr[da];
         bo = c.b_ptr[db];
@@ -169,11 +177,15 @@ struct ThreadPair {
             prev = r;
             while (nf >= 2 && int(fgap[nf - 1]) - 1 > g) merge_top(int(fgap[nf - 1]) - 1);
             if (nf >= 2 && int(fgap[nf - 1]) - 1 == g) merge_top(g);
+            if (bend >= cap) {  // the buffer is full: leave this pair to the warp kernel
+                overflow = true;
+                return 0.0f;
+            }
             fgap[nf] = uint8_t(g + 1);  // stored biased by one (the first frame has gap -1)
             fbeg[nf] = uint16_t(bend);
             fhead[nf] = uint16_t(bend);
             ++nf;
-            buf[bend++] = tentry(m, side, pay);
+            B(bend++) = tentry(m, side, pay);
         }
         while (nf >= 2) merge_top(int(fgap[nf - 1]) - 1);
         if (SAVE) c.count[pair] = saved;

@@ -529,6 +529,49 @@ extern "C" ft_status ft_quadtree_l1_dense(const ft_tree* t, const ft_docs* queri
 }
 
 namespace {
+// df of every query entry's node in the database index, summed
+__global__ void k_scan_matches(const uint32_t* __restrict__ q_ekey, int64_t n, const uint32_t* __restrict__ ukey,
+                               const uint32_t* __restrict__ uoff, int64_t n_ukeys,
+                               unsigned long long* __restrict__ total) {
+    unsigned long long acc = 0;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+        const uint32_t key = q_ekey[i];
+        int64_t lo = 0, hi = n_ukeys;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (ukey[mid] < key) lo = mid + 1; else hi = mid;
+        }
+        if (lo < n_ukeys && ukey[lo] == key) acc += uoff[lo + 1] - uoff[lo];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL_MASK, acc, o);
+    if (lane_id() == 0 && acc) atomicAdd(total, acc);
+}
+}  // namespace
+
+extern "C" ft_status ft_quadtree_scan_matches(const ft_tree* t, const ft_docs* queries, const ft_docs* db,
+                                              int64_t* matches_out_host) {
+    if (!t || !queries || !db || queries->tree != t || db->tree != t || !matches_out_host) return FT_EINVAL;
+    unsigned long long* d_total = nullptr;
+    FT_CUDA(cudaMalloc(&d_total, sizeof(unsigned long long)));
+    unsigned long long h = 0;
+    cudaError_t e = cudaMemset(d_total, 0, sizeof(unsigned long long));
+    if (e == cudaSuccess && queries->n_embed > 0) {
+        k_scan_matches<<<grid_for(queries->n_embed, 256), 256>>>(queries->d_ekey, queries->n_embed, db->d_ukey,
+                                                                 db->d_uoff, db->n_ukeys, d_total);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(&h, d_total, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(d_total);
+    if (e != cudaSuccess) {
+        ft_note_cuda_error(e, "ft_quadtree_scan_matches", __FILE__, __LINE__);
+        return FT_ECUDA;
+    }
+    *matches_out_host = int64_t(h);
+    return FT_OK;
+}
+
+namespace {
 size_t knn_layout(const ft_tree* t, const ft_docs* db, const ft_docs* q, int32_t k1, void* base, KnnLayout* out) {
     WsCarver w(base);
     KnnLayout l{};

@@ -214,3 +214,32 @@ def test_rejects_bad_inputs():
     o = out.cpu().numpy()
     assert np.isnan(o[0]) and o[1] == 0.0
     assert tree.status() == 0
+
+
+@pytest.mark.parametrize("name", ["grid", "tiny2d"])
+@pytest.mark.parametrize("cap", [32, 64])
+def test_thread_form_overflow_goes_to_warp_kernel(name, cap):
+    """Lane-per-pair form with item buffers too small for many pairs: those
+    pairs are finished by the warp-per-pair kernel; costs and saved flows stay
+    exact."""
+    pts, L, shift, db, q = CASES[name]
+    tree, otree = build_both(pts, L, shift)
+    tree.set_config(2, cap, 2)
+    Dd, Dq = api.Docs.from_csr(tree, db), api.Docs.from_csr(tree, q)
+    Sd, Sq = oracle_supports(otree, db), oracle_supports(otree, q)
+    got = api.flowtree_batch(tree, tree.points, Dq, Dd).cpu().numpy().astype(np.float64)
+    qa = np.repeat(np.arange(q.n), db.n)
+    qb = np.tile(np.arange(db.n), q.n)
+    np.testing.assert_allclose(got, _oracle_costs(otree, pts, Sq, Sd, qa, qb), rtol=REL, atol=1e-30)
+    rng = np.random.default_rng(7)
+    pa = rng.integers(0, db.n, 100)
+    pb = rng.integers(0, db.n, 100)
+    flows = api.Flows(tree, Dd, Dd, pa, pb)
+    api.flowtree_batch(tree, tree.points, Dd, Dd, flows.pair_a, flows.pair_b, flows=flows)
+    got_f = flows.export()
+    for i in range(100):
+        ia, ib, f, dep = otree.flow(*Sd.doc(pa[i]), *Sd.doc(pb[i]))
+        ref = sorted(zip(ia.tolist(), ib.tolist(), f.tolist(), dep.tolist()))
+        g = got_f[i]
+        assert sorted(zip(g[0].tolist(), g[1].tolist(), g[2].tolist(), g[3].tolist())) == ref, i
+    assert tree.status() == 0

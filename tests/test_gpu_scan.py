@@ -133,3 +133,21 @@ def test_l1_dense_many_tiles_and_ranges():
         want = O.topk_ids(row, 100)
         assert np.array_equal(ids[i].cpu().numpy(), want)
         assert np.array_equal(l1[i].cpu().numpy(), row[want])
+
+
+def test_scan_matches_count():
+    """The scan's work count: a document against itself matches each of its
+    embedding entries once, and counts add over a split of the database."""
+    pts, L, shift, db, q = WL["d300"]
+    tree = api.Tree(torch.as_tensor(pts, device="cuda"), L, shift)
+    Dq = api.Docs.from_csr(tree, q)
+    for i in range(q.n):
+        one = api.Docs.from_csr(tree, q.subset([i]))
+        assert api.quadtree_scan_matches(tree, one, one) == one.info.n_embed
+    half = db.n // 2
+    D = api.Docs.from_csr(tree, db)
+    D1 = api.Docs.from_csr(tree, db.subset(np.arange(half)))
+    D2 = api.Docs.from_csr(tree, db.subset(np.arange(half, db.n)))
+    m = api.quadtree_scan_matches(tree, Dq, D)
+    assert m == api.quadtree_scan_matches(tree, Dq, D1) + api.quadtree_scan_matches(tree, Dq, D2)
+    assert m > 0
