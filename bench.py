@@ -502,6 +502,21 @@ def extras(args, tree, D, Q, q_h, db_h, pts, shift, batched_value, dev, pk, pk_k
         except Exception as ex:  # report, do not lose the main line
             out["scale_knn_pipeline"] = {"error": "%s: %s" % (type(ex).__name__, ex)}
 
+    # random-model planted experiment (Sec. 4.2 model, Sec. 5.1 figure "Results on random data")
+    try:
+        from paper_1910_04126_gb300 import planted
+        t0 = time.time()
+        ns_a = [20, 50, 100, 1000, 10000, 100000] if not args.quick else [20, 100]
+        ns_b = [200, 1000, 3000] if not args.quick else [200]
+        pa_ = planted.run(ns_a, dim=10, s=10, eps=0.25, reps=100 if not args.quick else 10, seed=0)
+        pb_ = planted.run(ns_b, dim=10, s=100, eps=0.4, reps=30 if not args.quick else 5, seed=1)
+        out["planted_random_model"] = {
+            "competitors": "planted support vs all s(N-s) single swaps; success = strictly smallest score",
+            "d10_s10_eps0.25": pa_["results"], "d10_s100_eps0.4": pb_["results"],
+            "wall_s": time.time() - t0}
+    except Exception as ex:  # report, do not lose the main line
+        out["planted_random_model"] = {"error": "%s: %s" % (type(ex).__name__, ex)}
+
     # CPU oracle on the host cores (bounded sample of the same image workload)
     cores = os.cpu_count() or 1
     r_n, n_n, dt_n = oracle_rate(pts, shift, db_h, q_h, 12.0 if not args.quick else 2.0, cores, seed=1)

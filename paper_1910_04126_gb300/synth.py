@@ -305,3 +305,62 @@ def planted(n_points: int, dim: int, s: int, eps: float, seed: int):
     pts = np.concatenate([X, np.array(ys)], axis=0).astype(np.float32)
     query = np.arange(n_points, n_points + s)
     return pts, support.astype(np.int64), query.astype(np.int64)
+
+
+def sphere_cap_point(x: np.ndarray, eps: float, rng: np.random.Generator) -> np.ndarray:
+    """A point uniform on {y in S^(d-1) : ||y - x|| <= eps} (x a unit vector).
+
+    The angle t between y and x has density proportional to sin(t)^(d-2) on
+    [0, t_max], t_max = 2 asin(eps / 2) (drawn by rejection against the
+    uniform density); the direction orthogonal to x is uniform.
+    """
+    d = x.shape[0]
+    t_max = 2.0 * np.arcsin(min(eps, 2.0) / 2.0)
+    s_max = np.sin(min(t_max, np.pi / 2))
+    while True:
+        t = rng.random() * t_max
+        if d <= 2 or rng.random() <= (np.sin(t) / s_max) ** (d - 2):
+            break
+    v = rng.standard_normal(d)
+    v -= v.dot(x) * x
+    v /= np.linalg.norm(v)
+    y = x * np.cos(t) + v * np.sin(t)
+    return y / np.linalg.norm(y)
+
+
+def planted_instance(n_points: int, dim: int, s: int, eps: float, seed: int):
+    """One repetition of the random model of Sec. 4.2.
+
+    Ground set X: n_points i.i.d. uniform on S^(dim-1); a planted support of s
+    distinct points of X; the query support y_1..y_s, y_k uniform among the
+    points of the sphere within distance eps of x_k.  Returns (points float32
+    [n_points + s][dim] = X then the y's, planted support ids, query ids).
+    """
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((n_points, dim))
+    X /= np.linalg.norm(X, axis=1, keepdims=True)
+    support = rng.choice(n_points, size=s, replace=False)
+    Y = np.array([sphere_cap_point(X[k], eps, rng) for k in support])
+    pts = np.concatenate([X, Y], axis=0).astype(np.float32)
+    return pts, support.astype(np.int64), np.arange(n_points, n_points + s, dtype=np.int64)
+
+
+def single_swap_docs(support: np.ndarray, n_points: int) -> Docs:
+    """The planted support (document 0) and every support that differs from it
+    in one point: x_k replaced by any x' of the ground set outside the support
+    (documents 1 .. s (n_points - s), in order of k, then x').  Uniform
+    weights."""
+    support = np.asarray(support, dtype=np.int64)
+    s = len(support)
+    others = np.setdiff1d(np.arange(n_points, dtype=np.int64), support)
+    m = len(others)
+    words = np.empty((1 + s * m, s), dtype=np.int32)
+    words[0] = support
+    base = np.broadcast_to(support, (m, s))
+    for k in range(s):
+        block = base.copy()
+        block[:, k] = others
+        words[1 + k * m: 1 + (k + 1) * m] = block
+    n = words.shape[0]
+    return Docs(np.arange(0, n * s + 1, s, dtype=np.int64), words.reshape(-1).astype(np.int32),
+                np.ones(n * s, dtype=np.float32))
