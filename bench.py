@@ -496,6 +496,31 @@ def extras(args, tree, D, Q, q_h, db_h, pts, shift, batched_value, dev, pk, pk_k
         "workload": "vocab %d x 300, %d docs (log-normal lengths, Zipf(1.1) words), %d queries, top-%d -> top-%d"
                     % (nwt, ndb, nqt, k1, TOPK)}
 
+    # three-stage pipeline: quadtree -> top-1,000 -> Flowtree -> top-20 -> exact W1 -> top-10
+    try:
+        nq_x = 100 if not args.quick else 20
+        Qx3 = api.Docs.from_csr(t3, tq.subset(np.arange(nq_x)))
+        k2 = 2 * TOPK  # Flowtree as an intermediate stage keeps c = max(10, 2 c_next)
+        kx = min(k1, 1000)
+        wsx = torch.empty(api.knn_exact_workspace_size(t3, D3, Qx3, kx, k2, TOPK), dtype=torch.uint8, device=dev)
+        api.knn_exact(t3, t3.points, D3, Qx3, kx, k2, TOPK, workspace=wsx)
+        torch.cuda.synchronize()
+        e0.record()
+        ex_ids, ex_d = api.knn_exact(t3, t3.points, D3, Qx3, kx, k2, TOPK, workspace=wsx)
+        e1.record()
+        e1.synchronize()
+        msx = e0.elapsed_time(e1)
+        ft_ids, _ = api.knn(t3, t3.points, D3, Qx3, kx, TOPK)
+        a_, b_ = ex_ids.cpu().numpy(), ft_ids.cpu().numpy()
+        out["text_knn_exact_pipeline"] = {
+            "batch_ms": msx, "queries": nq_x, "k1": kx, "k2": k2, "k": TOPK,
+            "exact_pairs_per_s": nq_x * k2 / (msx * 1e-3),
+            "top10_overlap_with_flowtree_only": float(np.mean([len(set(x) & set(y)) / TOPK for x, y in zip(a_, b_)])),
+            "stage": "exact W1 by successive shortest paths, one warp per pair (ft_exact_w1_batch)"}
+        del wsx
+    except Exception as ex:  # report, do not lose the main line
+        out["text_knn_exact_pipeline"] = {"error": "%s: %s" % (type(ex).__name__, ex)}
+
     if not args.skip_scale:
         try:
             out["scale_knn_pipeline"] = scale_leg(args, dev, pk, pk_kind)

@@ -312,6 +312,45 @@ ft_status ft_knn(const ft_tree* t, const float* vocab_dev, const ft_docs* db, co
                  void* stream);
 
 /* ------------------------------------------------------------------------
+ * Exact W1 (Eq. 1) of document pairs: the re-ranking stage of the Sec. 5.2
+ * pipelines (the paper runs a network-simplex code on the CPU).
+ *
+ * For pair i, the min-cost transportation between the supports of
+ * a[pair_a_dev[i]] and b[pair_b_dev[i]] (their 2^24 fixed-point masses,
+ * equal totals) with arc cost ||x - y||_2 over the rows of vocab_dev
+ * float32 [n_points][dim] (the tree's ground set and dimension):
+ *   cost_out_dev[i] = sum f(x, y) ||x - y|| / 2^24.
+ * Solved per pair by one warp with successive shortest paths and node
+ * potentials (Dijkstra over the dense bipartite graph); the flow is exact
+ * integers, costs and potentials are FP32, so the value is optimal up to the
+ * FP32 rounding of the costs.  Time about (s_a + s_b)^3 / 32 warp steps per
+ * pair: meant for the few candidates that reach the last stage.
+ * a and b must share one tree.  pair arrays int32 [n_pairs] on the device
+ * (an index out of range flags FT_EINVAL in the status word and yields NaN).
+ * A pair that does not converge within 8 (s_a + s_b) + 64 augmentations
+ * (not expected) flags FT_ETIMEOUT and yields NaN.  Workspace per resident
+ * warp: 8 B x max_support(a) x max_support(b).  Allocation-free.
+ * ------------------------------------------------------------------------ */
+size_t ft_exact_w1_workspace_size(const ft_docs* a, const ft_docs* b, int64_t n_pairs);
+ft_status ft_exact_w1_batch(const float* vocab_dev, const ft_docs* a, const ft_docs* b, const int32_t* pair_a_dev,
+                            const int32_t* pair_b_dev, int64_t n_pairs, float* cost_out_dev, void* workspace,
+                            size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Three-stage nearest-neighbour pipeline (Sec. 5.2; Flowtree as the
+ * intermediate stage of Sec. 5.3's tuned pipelines): quadtree scan ->
+ * top-k1 -> batched Flowtree -> top-k2 -> exact W1 -> top-k per query.
+ * ids_out_dev int32 [nq][k], dist_out_dev float32 [nq][k] (exact W1),
+ * ascending by (W1, document id).  k <= k2 <= k1.  Allocation-free and
+ * synchronisation-free: capturable in a CUDA graph.
+ * ------------------------------------------------------------------------ */
+size_t ft_knn_exact_workspace_size(const ft_tree* t, const ft_docs* db, const ft_docs* queries, int32_t k1,
+                                   int32_t k2, int32_t k);
+ft_status ft_knn_exact(const ft_tree* t, const float* vocab_dev, const ft_docs* db, const ft_docs* queries,
+                       int32_t k1, int32_t k2, int32_t k, void* workspace, size_t ws_bytes, int32_t* ids_out_dev,
+                       float* dist_out_dev, void* stream);
+
+/* ------------------------------------------------------------------------
  * Per-row top-k of FP32 values (final selection, Sec. 5.2): for each of
  * n_rows rows of values_dev [n_rows][n_cols] (row-major, non-negative
  * values such as Flowtree costs), the k smallest ascending by (value,

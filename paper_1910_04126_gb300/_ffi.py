@@ -74,6 +74,10 @@ SIGNATURES = {
     "ft_quadtree_scan_matches": (i32, [vp, vp, vp, C.POINTER(i64)]),
     "ft_knn_workspace_size": (sz, [vp, vp, vp, i32, i32]),
     "ft_knn": (i32, [vp, vp, vp, vp, i32, i32, vp, sz, vp, vp, vp]),
+    "ft_exact_w1_workspace_size": (sz, [vp, vp, i64]),
+    "ft_exact_w1_batch": (i32, [vp, vp, vp, vp, vp, i64, vp, vp, sz, vp]),
+    "ft_knn_exact_workspace_size": (sz, [vp, vp, vp, i32, i32, i32]),
+    "ft_knn_exact": (i32, [vp, vp, vp, vp, i32, i32, i32, vp, sz, vp, vp, vp]),
     "ft_topk_f32_workspace_size": (sz, [i64, i64]),
     "ft_topk_f32": (i32, [vp, i64, i64, i32, vp, sz, vp, vp, vp]),
     "ft_flowtree_batch_static": (i32, [vp, vp, vp, vp, vp, vp, i64, vp, vp]),

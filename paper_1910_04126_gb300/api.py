@@ -340,6 +340,47 @@ def knn(tree: Tree, vocab: torch.Tensor, db: Docs, queries: Docs, k1: int, k: in
     return ids, dist
 
 
+def exact_w1_workspace_size(a: Docs, b: Docs, n_pairs: int) -> int:
+    return int(_ffi.load().ft_exact_w1_workspace_size(a.handle, b.handle, n_pairs))
+
+
+def exact_w1(tree: Tree, vocab: torch.Tensor, a: Docs, b: Docs, pair_a, pair_b,
+             out: Optional[torch.Tensor] = None, workspace: Optional[torch.Tensor] = None, stream=None):
+    """Exact W1 of the pairs (a[pair_a[i]], b[pair_b[i]]) by min-cost flow (ft_exact_w1_batch)."""
+    lib = _ffi.load()
+    pa = _dev(pair_a, torch.int32, tree.device)
+    pb = _dev(pair_b, torch.int32, tree.device)
+    n = int(pa.numel())
+    if out is None:
+        out = torch.empty(n, dtype=torch.float32, device=tree.device)
+    ws = _workspace(exact_w1_workspace_size(a, b, n), tree.device, workspace)
+    code = lib.ft_exact_w1_batch(_ptr(vocab), a.handle, b.handle, _ptr(pa), _ptr(pb), n, _ptr(out), _ptr(ws),
+                                 ws.numel(), _stream(stream))
+    check(code, "ft_exact_w1_batch")
+    return out
+
+
+def knn_exact_workspace_size(tree: Tree, db: Docs, queries: Docs, k1: int, k2: int, k: int) -> int:
+    return int(_ffi.load().ft_knn_exact_workspace_size(tree.handle, db.handle, queries.handle, k1, k2, k))
+
+
+def knn_exact(tree: Tree, vocab: torch.Tensor, db: Docs, queries: Docs, k1: int, k2: int, k: int,
+              workspace: Optional[torch.Tensor] = None, ids: Optional[torch.Tensor] = None,
+              dist: Optional[torch.Tensor] = None, stream=None):
+    """Quadtree scan -> top-k1 -> Flowtree -> top-k2 -> exact W1 -> top-k per query (ft_knn_exact)."""
+    lib = _ffi.load()
+    nq = queries.n_docs
+    if ids is None:
+        ids = torch.empty((nq, k), dtype=torch.int32, device=tree.device)
+    if dist is None:
+        dist = torch.empty((nq, k), dtype=torch.float32, device=tree.device)
+    ws = _workspace(knn_exact_workspace_size(tree, db, queries, k1, k2, k), tree.device, workspace)
+    code = lib.ft_knn_exact(tree.handle, _ptr(vocab), db.handle, queries.handle, k1, k2, k, _ptr(ws), ws.numel(),
+                            _ptr(ids), _ptr(dist), _stream(stream))
+    check(code, "ft_knn_exact")
+    return ids, dist
+
+
 def topk_f32(values: torch.Tensor, k: int, ids: Optional[torch.Tensor] = None,
              vals: Optional[torch.Tensor] = None, workspace: Optional[torch.Tensor] = None, stream=None):
     """Per-row k smallest of a [rows, cols] FP32 tensor, ties by column (ft_topk_f32)."""

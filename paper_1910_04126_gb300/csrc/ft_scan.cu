@@ -614,6 +614,73 @@ extern "C" ft_status ft_knn(const ft_tree* t, const float* vocab_dev, const ft_d
     return FT_OK;
 }
 
+namespace {
+struct KnnExactLayout {
+    KnnLayout knn;
+    int32_t* ids2;   // [nq][k2] Flowtree survivors
+    float* dist2;    // [nq][k2] their Flowtree values (unused downstream)
+    int32_t* pa2;    // [nq * k2] exact-stage pairs
+    int32_t* pb2;
+    float* cost2;    // [nq * k2] exact W1
+    void* ews;
+    size_t ews_bytes;
+};
+
+size_t knn_exact_layout(const ft_tree* t, const ft_docs* db, const ft_docs* q, int32_t k1, int32_t k2, void* base,
+                        KnnExactLayout* out) {
+    KnnExactLayout l{};
+    const size_t knn_bytes = (knn_layout(t, db, q, k1, base, base ? &l.knn : nullptr) + 255) & ~size_t(255);
+    WsCarver w(base ? static_cast<char*>(base) + knn_bytes : nullptr);  // 256-byte aligned like the rest
+    const int64_t np2 = q->n_docs * int64_t(k2);
+    l.ids2 = w.take<int32_t>(size_t(np2));
+    l.dist2 = w.take<float>(size_t(np2));
+    l.pa2 = w.take<int32_t>(size_t(np2));
+    l.pb2 = w.take<int32_t>(size_t(np2));
+    l.cost2 = w.take<float>(size_t(np2));
+    l.ews_bytes = ft_exact_w1_workspace_size(q, db, np2);
+    l.ews = w.take<uint8_t>(l.ews_bytes);
+    if (out) *out = l;
+    return knn_bytes + w.off + 256;
+}
+}  // namespace
+
+extern "C" size_t ft_knn_exact_workspace_size(const ft_tree* t, const ft_docs* db, const ft_docs* queries, int32_t k1,
+                                              int32_t k2, int32_t k) {
+    if (check_scan(t, queries, db, k1) != FT_OK || k < 1 || k > k2 || k2 > k1) return 0;
+    if (ft_exact_w1_workspace_size(queries, db, queries->n_docs * int64_t(k2)) == 0) return 0;
+    return knn_exact_layout(t, db, queries, k1, k2, nullptr, nullptr);
+}
+
+extern "C" ft_status ft_knn_exact(const ft_tree* t, const float* vocab_dev, const ft_docs* db, const ft_docs* queries,
+                                  int32_t k1, int32_t k2, int32_t k, void* workspace, size_t ws_bytes,
+                                  int32_t* ids_out_dev, float* dist_out_dev, void* stream) {
+    FT_TRY(check_scan(t, queries, db, k1));
+    if (!vocab_dev || !ids_out_dev || !dist_out_dev || k < 1 || k > k2 || k2 > k1) return FT_EINVAL;
+    if (ft_exact_w1_workspace_size(queries, db, queries->n_docs * int64_t(k2)) == 0) return FT_EUNSUPPORTED;
+    if (!workspace || ws_bytes < knn_exact_layout(t, db, queries, k1, k2, nullptr, nullptr)) return FT_EWORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    KnnExactLayout l;
+    knn_exact_layout(t, db, queries, k1, k2, workspace, &l);
+    const int64_t nq = queries->n_docs, np = nq * int64_t(k1), np2 = nq * int64_t(k2);
+    // stage 1: quadtree scan -> top-k1
+    FT_TRY(launch_scan(t, queries, db, l.knn.keys, nullptr, s));
+    k_select_u64<false><<<unsigned(nq), SEL_THREADS, 0, s>>>(l.knn.keys, db->n_docs, k1, l.knn.cand, nullptr, nullptr,
+                                                             t->d_status);
+    // stage 2: Flowtree on the k1 candidates -> top-k2
+    k_knn_pairs<<<grid_for(np, 256), 256, 0, s>>>(l.knn.cand, nq, k1, l.knn.pa, l.knn.pb);
+    FT_CUDA(cudaGetLastError());
+    FT_TRY(ft_flowtree_batch(t, vocab_dev, queries, db, l.knn.pa, l.knn.pb, np, l.knn.cost, nullptr, l.knn.fws,
+                             l.knn.fws_bytes, s));
+    k_final_topk<<<unsigned(nq), SEL_THREADS, 0, s>>>(l.knn.cost, l.knn.cand, k1, k2, l.ids2, l.dist2);
+    // stage 3: exact W1 on the k2 survivors -> top-k
+    k_knn_pairs<<<grid_for(np2, 256), 256, 0, s>>>(l.ids2, nq, k2, l.pa2, l.pb2);
+    FT_CUDA(cudaGetLastError());
+    FT_TRY(ft_exact_w1_batch(vocab_dev, queries, db, l.pa2, l.pb2, np2, l.cost2, l.ews, l.ews_bytes, s));
+    k_final_topk<<<unsigned(nq), SEL_THREADS, 0, s>>>(l.cost2, l.ids2, k2, k, ids_out_dev, dist_out_dev);
+    FT_CUDA(cudaGetLastError());
+    return FT_OK;
+}
+
 extern "C" size_t ft_topk_f32_workspace_size(int64_t n_rows, int64_t n_cols) {
     if (n_rows < 1 || n_cols < 1) return 0;
     WsCarver w(nullptr);
