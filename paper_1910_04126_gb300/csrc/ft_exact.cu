@@ -55,11 +55,15 @@ struct ExactCtx {
     float* cmat;        // per warp [slice] cost matrix, row-major [na][nb]
     uint32_t* flow;     // per warp [slice] flow, row-major [na][nb]
     size_t slice;       // entries per warp slice (>= max_a * max_b)
+    uint32_t* fbits;    // per warp [bslice] bitmap of arcs with flow, column-major: [nb][ceil(na/32)] words
+    size_t bslice;
     int nmax;           // max_a + max_b: node arrays per warp
     const uint32_t* order;  // queue position -> pair, largest pairs first
     unsigned long long* queue;
     uint32_t* status;
 };
+
+__device__ __forceinline__ bool settled(float d) { return (__float_as_uint(d) >> 31) != 0u; }
 
 __device__ __forceinline__ void warp_argmin(float& v, int& i) {
 #pragma unroll
@@ -75,12 +79,14 @@ __device__ __forceinline__ void warp_argmin(float& v, int& i) {
 
 // Solves one pair with the calling warp; returns W1 (all lanes), or NaN
 // after flagging the status word when the phase limit is reached.
-__device__ float exact_pair(const ExactCtx& c, int64_t da, int64_t db, float* cm, uint32_t* fl, float* dist,
-                            float* pi, int16_t* pred, uint8_t* done, uint32_t* resid) {
+__device__ float exact_pair(const ExactCtx& c, int64_t da, int64_t db, float* cm, uint32_t* fl, uint32_t* fb,
+                            float* dist, float* pi, int16_t* pred, uint32_t* resid) {
     const unsigned lane = lane_id();
     const int64_t ao = c.a_ptr[da], bo = c.b_ptr[db];
     const int na = int(c.a_ptr[da + 1] - ao), nb = int(c.b_ptr[db + 1] - bo);
     const int n = na + nb;
+    const int W = (na + 31) >> 5;  // bitmap words per demand node
+    for (int e = int(lane); e < nb * W; e += 32) fb[e] = 0u;
     // cost matrix (direct differences in FP32: no cancellation for near points)
     for (int i = 0; i < na; ++i) {
         const float* x = c.vocab + size_t(c.a_word[ao + i]) * c.dim;
@@ -115,6 +121,7 @@ __device__ float exact_pair(const ExactCtx& c, int64_t da, int64_t db, float* cm
         if (lo < nb && c.b_rank[bo + lo] == r) {
             const uint32_t f = min(resid[i], resid[na + lo]);
             fl[size_t(i) * nb + lo] = f;
+            if (f) atomicOr(fb + size_t(lo) * W + (i >> 5), 1u << (i & 31));
             resid[i] -= f;
             resid[na + lo] -= f;
         }
@@ -131,11 +138,12 @@ __device__ float exact_pair(const ExactCtx& c, int64_t da, int64_t db, float* cm
             failed = true;
             break;
         }
-        // Dijkstra on reduced costs from every supply node with supply left
+        // Dijkstra on reduced costs from every supply node with supply left.
+        // A settled node keeps its distance with the sign bit set (-0.0 for
+        // 0), so one load tells both.
         for (int v = int(lane); v < n; v += 32) {
             dist[v] = (v < na && resid[v] > 0) ? 0.0f : FLT_MAX;
             pred[v] = -1;
-            done[v] = 0;
         }
         __syncwarp();
         int t = -1;
@@ -143,18 +151,23 @@ __device__ float exact_pair(const ExactCtx& c, int64_t da, int64_t db, float* cm
         for (int step = 0; step < n; ++step) {
             float best = FLT_MAX;
             int bi = 0x7fffffff;
-            for (int v = int(lane); v < n; v += 32) {
+            int v = int(lane);
+            for (; v + 96 < n; v += 128) {  // four independent loads in flight
+                const float d0 = dist[v], d1 = dist[v + 32], d2 = dist[v + 64], d3 = dist[v + 96];
+                if (!settled(d0) && d0 < best) { best = d0; bi = v; }
+                if (!settled(d1) && d1 < best) { best = d1; bi = v + 32; }
+                if (!settled(d2) && d2 < best) { best = d2; bi = v + 64; }
+                if (!settled(d3) && d3 < best) { best = d3; bi = v + 96; }
+            }
+            for (; v < n; v += 32) {
                 const float dv = dist[v];
-                if (!done[v] && dv < best) {
-                    best = dv;
-                    bi = v;
-                }
+                if (!settled(dv) && dv < best) { best = dv; bi = v; }
             }
             warp_argmin(best, bi);
             if (best == FLT_MAX) break;  // nothing reachable (cannot happen: totals are equal)
             const int u = bi;
             __syncwarp();
-            if (lane == 0) done[u] = 1;
+            if (lane == 0) dist[u] = -best;
             if (u >= na && resid[u] > 0) {
                 t = u;
                 D = best;
@@ -164,23 +177,43 @@ __device__ float exact_pair(const ExactCtx& c, int64_t da, int64_t db, float* cm
             const float pu = pi[u];
             if (u < na) {  // forward arcs u -> every demand node
                 const float* row = cm + size_t(u) * nb;
-                for (int j = int(lane); j < nb; j += 32) {
-                    const int v = na + j;
-                    if (done[v]) continue;
-                    const float nd = best + fmaxf(0.0f, row[j] + pu - pi[v]);
-                    if (nd < dist[v]) {
-                        dist[v] = nd;
-                        pred[v] = int16_t(u);
+                int j = int(lane);
+                for (; j + 32 < nb; j += 64) {  // two rows entries, their loads in flight together
+                    const float c0 = row[j], c1 = row[j + 32];
+                    const float q0 = pi[na + j], q1 = pi[na + j + 32];
+                    const float e0 = dist[na + j], e1 = dist[na + j + 32];
+                    const float n0 = best + fmaxf(0.0f, c0 + pu - q0), n1 = best + fmaxf(0.0f, c1 + pu - q1);
+                    if (!settled(e0) && n0 < e0) {
+                        dist[na + j] = n0;
+                        pred[na + j] = int16_t(u);
+                    }
+                    if (!settled(e1) && n1 < e1) {
+                        dist[na + j + 32] = n1;
+                        pred[na + j + 32] = int16_t(u);
                     }
                 }
-            } else {  // backward arcs: demand node u -> supply nodes that ship to it
+                for (; j < nb; j += 32) {
+                    const float e0 = dist[na + j];
+                    const float n0 = best + fmaxf(0.0f, row[j] + pu - pi[na + j]);
+                    if (!settled(e0) && n0 < e0) {
+                        dist[na + j] = n0;
+                        pred[na + j] = int16_t(u);
+                    }
+                }
+            } else {  // backward arcs: demand node u -> supply nodes that ship to it (bitmap)
                 const int j = u - na;
-                for (int i = int(lane); i < na; i += 32) {
-                    if (done[i] || fl[size_t(i) * nb + j] == 0u) continue;
-                    const float nd = best + fmaxf(0.0f, pu - cm[size_t(i) * nb + j] - pi[i]);
-                    if (nd < dist[i]) {
-                        dist[i] = nd;
-                        pred[i] = int16_t(u);
+                for (int w = int(lane); w < W; w += 32) {
+                    uint32_t m = fb[size_t(j) * W + w];
+                    while (m) {
+                        const int i = w * 32 + __ffs(m) - 1;
+                        m &= m - 1;
+                        const float di = dist[i];
+                        if (settled(di)) continue;
+                        const float nd = best + fmaxf(0.0f, pu - cm[size_t(i) * nb + j] - pi[i]);
+                        if (nd < di) {
+                            dist[i] = nd;
+                            pred[i] = int16_t(u);
+                        }
                     }
                 }
             }
@@ -190,7 +223,10 @@ __device__ float exact_pair(const ExactCtx& c, int64_t da, int64_t db, float* cm
             failed = true;
             break;
         }
-        for (int v = int(lane); v < n; v += 32) pi[v] += fminf(dist[v], D);
+        for (int v = int(lane); v < n; v += 32) {
+            const float dv = dist[v];
+            pi[v] += settled(dv) ? -dv : fminf(dv, D);
+        }
         __syncwarp();
         // augment along the path (one lane; the path has at most n arcs)
         uint32_t delta = 0;
@@ -208,8 +244,15 @@ __device__ float exact_pair(const ExactCtx& c, int64_t da, int64_t db, float* cm
             guard = 0;
             while (pred[v] >= 0 && guard++ < n) {
                 const int u = pred[v];
-                if (u < na) fl[size_t(u) * nb + (v - na)] += delta;  // forward arc u -> v
-                else fl[size_t(v) * nb + (u - na)] -= delta;         // backward arc u -> v
+                if (u < na) {  // forward arc u -> v
+                    uint32_t& f = fl[size_t(u) * nb + (v - na)];
+                    if (f == 0u) fb[size_t(v - na) * W + (u >> 5)] |= 1u << (u & 31);
+                    f += delta;
+                } else {       // backward arc u -> v
+                    uint32_t& f = fl[size_t(v) * nb + (u - na)];
+                    f -= delta;
+                    if (f == 0u) fb[size_t(u - na) * W + (v >> 5)] &= ~(1u << (v & 31));
+                }
                 v = u;
             }
             resid[s] -= delta;
@@ -248,10 +291,10 @@ __global__ void __launch_bounds__(EX_WARPS * 32) k_exact_w1(ExactCtx c) {
     float* pi = dist + nm;
     uint32_t* resid = reinterpret_cast<uint32_t*>(pi + nm);
     int16_t* pred = reinterpret_cast<int16_t*>(resid + nm);
-    uint8_t* done = reinterpret_cast<uint8_t*>(pred + nm);
     const int64_t gw = int64_t(blockIdx.x) * EX_WARPS + warp;
     float* cm = c.cmat + size_t(gw) * c.slice;
     uint32_t* fl = c.flow + size_t(gw) * c.slice;
+    uint32_t* fb = c.fbits + size_t(gw) * c.bslice;
     for (;;) {
         unsigned long long q = 0;
         if (lane == 0) q = atomicAdd(c.queue, 1ull);
@@ -266,7 +309,7 @@ __global__ void __launch_bounds__(EX_WARPS * 32) k_exact_w1(ExactCtx c) {
             }
             continue;
         }
-        const float w = exact_pair(c, da, db, cm, fl, dist, pi, pred, done, resid);
+        const float w = exact_pair(c, da, db, cm, fl, fb, dist, pi, pred, resid);
         if (lane == 0) c.cost_out[p] = w;
     }
 }
@@ -276,6 +319,7 @@ struct ExactPlan {
     int blocks = 0;
     size_t smem = 0;
     size_t slice = 0;
+    size_t bslice = 0;
     int nmax = 0;
 };
 
@@ -285,7 +329,8 @@ ft_status plan_exact(const ft_docs* a, const ft_docs* b, int64_t n_pairs, ExactP
     p->nmax = (max_a + max_b + 31) & ~31;
     if (p->nmax > 32767) return FT_EUNSUPPORTED;  // node ids are int16 in the path records
     p->slice = (size_t(max_a) * max_b + 63) & ~size_t(63);
-    p->smem = size_t(EX_WARPS) * size_t(p->nmax) * 16;
+    p->bslice = (size_t(max_b) * ((max_a + 31) / 32) + 63) & ~size_t(63);
+    p->smem = size_t(EX_WARPS) * size_t(p->nmax) * 16;  // dist, pi, resid (4 B), pred (2 B) per node
     int dev = 0, max_smem = 0, sms = 0;
     FT_CUDA(cudaGetDevice(&dev));
     FT_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
@@ -307,6 +352,7 @@ struct ExactLayout {
     void* sort_tmp;
     float* cmat;
     uint32_t* flow;
+    uint32_t* fbits;
 };
 
 // sort key of a pair: larger supports first (the work grows like their
@@ -332,6 +378,7 @@ size_t exact_layout(const ExactPlan& p, void* base, ExactLayout* out) {
     const size_t per = size_t(p.blocks) * EX_WARPS * p.slice;
     l.cmat = w.take<float>(per);
     l.flow = w.take<uint32_t>(per);
+    l.fbits = w.take<uint32_t>(size_t(p.blocks) * EX_WARPS * p.bslice);
     if (out) *out = l;
     return w.off + 256;
 }
@@ -383,6 +430,8 @@ extern "C" ft_status ft_exact_w1_batch(const float* vocab_dev, const ft_docs* a,
     c.cmat = l.cmat;
     c.flow = l.flow;
     c.slice = p.slice;
+    c.fbits = l.fbits;
+    c.bslice = p.bslice;
     c.nmax = p.nmax;
     c.queue = l.queue;
     c.order = l.order;
