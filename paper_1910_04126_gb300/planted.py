@@ -14,8 +14,10 @@ support (x_k replaced by another point of X): Quadtree fails exactly when a
 cell holding x_k and y_k holds another point, i.e. when such a swap ties or
 beats the planted document.  The experiment therefore ranks the planted
 document against all s (N - s) single swaps; "success" = the planted
-document's score is strictly the smallest.  For Flowtree this is a necessary
-condition for success over the whole dataset.
+document's score is strictly the smallest (a tie is a failure: the method
+cannot tell the documents apart); the rate at which it is among the
+minimisers is reported too.  For Flowtree this is a necessary condition for
+success over the whole dataset.
 
 Every repetition draws a new instance and a new random shift of the tree;
 both scores come from the library (ft_quadtree_l1_dense, ft_flowtree_batch).
@@ -36,7 +38,7 @@ def run(n_points_list, dim: int = 10, s: int = 10, eps: float = 0.25, reps: int 
     dev = torch.device(device)
     out = []
     for n in n_points_list:
-        ok_qt = ok_ft = 0
+        ok_qt = ok_ft = tie_qt = tie_ft = 0
         pairs = 0
         gpu_s = 0.0
         for r in range(reps):
@@ -56,12 +58,15 @@ def run(n_points_list, dim: int = 10, s: int = 10, eps: float = 0.25, reps: int 
             l1, cost = l1.cpu().numpy(), cost.cpu().numpy()
             ok_qt += int(l1[0] < l1[1:].min())
             ok_ft += int(cost[0] < cost[1:].min())
+            tie_qt += int(l1[0] <= l1[1:].min())
+            tie_ft += int(cost[0] <= cost[1:].min())
             pairs += cand.n
             status = tree.status()
             if status != 0:
                 raise RuntimeError("device status %d in the planted experiment (N=%d, rep %d)" % (status, n, r))
         out.append({"n_points": int(n), "candidates_per_query": 1 + s * (int(n) - s),
                     "quadtree_success": ok_qt / reps, "flowtree_success": ok_ft / reps,
+                    "quadtree_among_minimizers": tie_qt / reps, "flowtree_among_minimizers": tie_ft / reps,
                     "pairs_scored": pairs, "gpu_seconds": gpu_s})
     return {"dim": dim, "s": s, "eps": eps, "reps": reps, "levels": levels, "results": out}
 
