@@ -388,9 +388,8 @@ def main():
                                      "picked_by": "ft_flowtree_autotune"}},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": statistics.mean(e2e_ms)},
-        # per step: the Flowtree launch (plus the warp launch for overflow
-        # pairs when the lane-per-pair form runs), then keys + select
-        "gpu_launches": (4 if tuned[2] == 2 else 3) * args.steps,
+        # per step: the Flowtree launch, then keys + select
+        "gpu_launches": 3 * args.steps,
         "clocks": clocks,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": alu_peak / 1e12, "unit": "Tops/s",
                      "frac": achieved / alu_peak, "traffic": traffic,

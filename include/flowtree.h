@@ -213,13 +213,11 @@ ft_status ft_flowtree_plain(const ft_tree* t, const float* vocab_dev, const ft_d
  *   algo          : FT_ALGO_AUTO, FT_ALGO_WARP (a warp per pair, level by
  *                   level over the merged supports staged in shared memory)
  *                   or FT_ALGO_THREAD (a thread per pair, one sweep with a
- *                   stack of open tree nodes, its item buffer in shared
- *                   memory; pairs that outgrow the buffer are finished by
- *                   the warp form in a second launch; dim <= 8 only).
- *                   AUTO = WARP; ft_flowtree_autotune picks either.
+ *                   stack of open tree nodes, its per-position state as bit
+ *                   arrays in shared memory; dim <= 8 only).  AUTO = WARP;
+ *                   ft_flowtree_autotune picks either.
  *   warps_per_cta : warps per CTA (1..8).
- *   stage_items   : WARP: merged support items each warp stages on chip.
- *                   THREAD: item buffer entries per thread (8 B each).
+ *   stage_items   : merged support items each warp stages on chip (WARP).
  *   stage_tables  : 1 = copy the vocabulary and the LCA table into shared
  *                   memory per CTA when they fit (at most 32 KiB); 0 = read
  *                   them through L1 (the default: one cached copy per SM

@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(256) k_flowtree_persistent(FlowCtx c, int cap,
     const int64_t gw = int64_t(blockIdx.x) * (blockDim.x >> 5) + warp;
     WarpBuf gbuf = sbuf;
     if (c.gscratch) gbuf = carve_warpbuf(c.gscratch + size_t(gw) * c.gscratch_warp_bytes, c.gscratch_items);
-    const int64_t n_pairs = c.n_dev ? int64_t(*c.n_dev) : c.n_pairs;
+    const int64_t n_pairs = c.n_pairs;
     for (;;) {
         unsigned long long first = 0;
         if (lane == 0) first = atomicAdd(reinterpret_cast<unsigned long long*>(c.queue), (unsigned long long)grab);
@@ -56,47 +56,63 @@ __global__ void __launch_bounds__(256) k_flowtree_persistent(FlowCtx c, int cap,
     }
 }
 
-// A lane per pair (low-dimensional ground sets).  The vocabulary and the LCA
-// table are copied to shared memory when they fit; each warp takes 32
-// consecutive queue entries at a time, and every lane sweeps its own pair with
-// a `cap`-entry item buffer in shared memory (lane-interleaved).  A pair that
-// needs more is appended to ovf (count in *n_ovf) for the warp kernel.
-// Dynamic shared memory: [tables (if staged)] [warps][cap][32] uint64.
+// A thread per pair (low-dimensional ground sets).  The vocabulary and the
+// LCA table are copied to shared memory when they fit.  Every lane runs the
+// sweep of its own pair one state-machine step per iteration; a lane whose
+// pair is done takes the next queue entry (one atomic per warp and
+// iteration).  Dynamic shared memory: [tables (if staged)]
+// [warps][lane_words(nmax)][32] uint32; gres: nmax residual words per thread.
 template <bool SAVE>
-__global__ void __launch_bounds__(256) k_flowtree_thread(FlowCtx c, int cap, int tables_bytes, uint32_t* ovf,
-                                                         unsigned int* n_ovf) {
+__global__ void __launch_bounds__(256) k_flowtree_thread(const __grid_constant__ FlowCtx c, int W, int tables_bytes,
+                                                         uint32_t* gres, int nmax) {
     extern __shared__ __align__(16) uint8_t smem[];
     const Tables tb = tables_bytes > 0 ? stage_tables(c, smem) : Tables{c.vocab, c.rmq};
     const unsigned lane = lane_id();
-    uint64_t* buf = reinterpret_cast<uint64_t*>(smem + tables_bytes) + size_t(threadIdx.x >> 5) * cap * 32 + lane;
+    const int words = 4 * W + 1 + 2 * kLaneFrames;
+    uint32_t* base = reinterpret_cast<uint32_t*>(smem + tables_bytes) + size_t(threadIdx.x >> 5) * words * 32 + lane;
+    const int64_t gt = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    LaneSweep<SAVE> sw(c, tb, base, W, gres + size_t(gt) * nmax);
+    int64_t pair = -1;
+    bool active = false, drained = false;
     for (;;) {
-        __syncwarp();
-        unsigned long long first = 0;
-        if (lane == 0) first = atomicAdd(reinterpret_cast<unsigned long long*>(c.queue), 32ull);
-        first = __shfl_sync(FULL_MASK, first, 0);
-        if (first >= (unsigned long long)c.n_pairs) break;
-        const int64_t q = int64_t(first) + lane;
-        if (q >= c.n_pairs) continue;  // no warp-wide operation follows before the next __syncwarp
-        const int64_t pair = c.order ? int64_t(c.order[q]) : q;
-        int64_t da, db;
-        if (c.pair_a) {
-            da = c.pair_a[pair];
-            db = c.pair_b[pair];
-        } else {
-            da = pair / c.nb_cross;
-            db = pair - da * c.nb_cross;
+        const unsigned need = __ballot_sync(FULL_MASK, !active);
+        if (need && !drained) {
+            const int leader = __ffs(need) - 1;
+            unsigned long long first = 0;
+            if (int(lane) == leader)
+                first = atomicAdd(reinterpret_cast<unsigned long long*>(c.queue), (unsigned long long)__popc(need));
+            first = __shfl_sync(FULL_MASK, first, leader);
+            if (first + __popc(need) >= (unsigned long long)c.n_pairs) drained = true;
+            if (!active) {
+                const int64_t q = int64_t(first) + __popc(need & lanemask_lt());
+                if (q < c.n_pairs) {
+                    pair = c.order ? int64_t(c.order[q]) : q;
+                    int64_t da, db;
+                    if (c.pair_a) {
+                        da = c.pair_a[pair];
+                        db = c.pair_b[pair];
+                    } else {
+                        da = pair / c.nb_cross;
+                        db = pair - da * c.nb_cross;
+                    }
+                    if (da < 0 || da >= c.na_docs || db < 0 || db >= c.nb_docs) {
+                        ft_flag(c.status, FT_DEV_EINVAL);
+                        c.cost_out[pair] = __int_as_float(0x7fc00000);
+                    } else {
+                        sw.start(pair, da, db);
+                        active = true;
+                    }
+                }
+            }
         }
-        if (da < 0 || da >= c.na_docs || db < 0 || db >= c.nb_docs) {
-            ft_flag(c.status, FT_DEV_EINVAL);
-            c.cost_out[pair] = __int_as_float(0x7fc00000);
-            continue;
-        }
-        ThreadPair<SAVE> tp(c, tb, buf, cap);
-        const float cost = tp.run(pair, da, db);
-        if (tp.overflow) {
-            ovf[atomicAdd(n_ovf, 1u)] = uint32_t(pair);
-        } else {
-            c.cost_out[pair] = cost;
+        if (!__any_sync(FULL_MASK, active) && drained) break;
+        if (active) {
+            sw.step();
+            if (sw.phase == LP_DONE) {
+                c.cost_out[pair] = sw.P.acc.value() * (1.0f / 16777216.0f);
+                if (SAVE) c.count[pair] = sw.P.saved;
+                active = false;
+            }
         }
     }
 }
@@ -187,14 +203,14 @@ struct Plan {
     int tables_bytes = 0;  // vocabulary + LCA table staged in shared memory (0 = read from global)
     // thread algorithm: the lane-per-pair launch; cap, warps, blocks, smem
     // above then describe the warp-per-pair launch for its overflow pairs
-    int tcap = 0;          // item buffer entries per lane
+    int tw = 0;            // words per bit array of a lane (positions up to the longest pair)
+    int tmaxn = 0;         // positions per thread (the longest pair)
     int twarps = 0;
     int tblocks = 0;
     size_t tsmem = 0;
 };
 
-constexpr int kThreadMaxItems = 2048;
-constexpr int kThreadDefaultCap = 256;
+constexpr int kThreadMaxItems = 8192;
 constexpr size_t kTablesMax = 32 * 1024;  // stage the tables when they are at most this big
 
 int staged_tables_bytes(const ft_tree* t) {
@@ -246,20 +262,17 @@ ft_status make_plan(const ft_tree* t, const ft_docs* a, const ft_docs* b, int64_
     ft_flowtree_config wcfg = cfg;
     if (p->algo == FT_ALGO_THREAD) {
         if (!thread_ok) return FT_EUNSUPPORTED;
-        // lane per pair: stage_items = item buffer entries per lane
-        p->tcap = std::max(32, std::min(cfg.stage_items > 0 ? cfg.stage_items : kThreadDefaultCap, maxn));
-        // default: as many warps (up to 4) as the buffers leave room for
-        const int fit = int((size_t(max_smem) - size_t(p->tables_bytes)) / (size_t(p->tcap) * 32 * 8));
-        p->twarps = cfg.warps_per_cta > 0 ? cfg.warps_per_cta : std::max(1, std::min(kDefaultWarps, fit));
-        p->tsmem = size_t(p->tables_bytes) + size_t(p->twarps) * p->tcap * 32 * 8;
+        p->tw = (maxn + 31) / 32;
+        p->tmaxn = maxn;
+        const size_t per_warp = size_t(lane_words(maxn)) * 32 * 4;
+        p->twarps = cfg.warps_per_cta > 0 ? cfg.warps_per_cta : 4;
+        p->tsmem = size_t(p->tables_bytes) + size_t(p->twarps) * per_warp;
         if (p->tsmem > size_t(max_smem)) return FT_EUNSUPPORTED;
         int bps = 0;
         FT_TRY(ft_prepare_kernel(thread_kernel(save), p->twarps * 32, p->tsmem, &bps));
         if (bps < 1) return FT_EUNSUPPORTED;
         p->tblocks = sms * bps;
-        // the warp launch for the overflow pairs: default shape
-        wcfg = {kDefaultWarps, 0, FT_ALGO_WARP, cfg.stage_tables};
-        p->warps = kDefaultWarps;
+        return FT_OK;
     }
     int cap = wcfg.stage_items > 0 ? round32(wcfg.stage_items) : std::min(maxn, 512);
     cap = std::min(cap, kMaxStage);
@@ -279,8 +292,8 @@ ft_status make_plan(const ft_tree* t, const ft_docs* a, const ft_docs* b, int64_
 }
 
 struct WsLayout {
-    unsigned int* queue;  // [0..1] queue, [2..3] overflow queue, [4] overflow count
-    uint32_t* ovf;        // thread algorithm: pairs left to the warp kernel
+    unsigned int* queue;
+    uint32_t* gres;       // thread algorithm: residuals of partly matched items, per thread
     uint32_t* order;
     uint32_t* keys;
     void* sort_tmp;
@@ -290,8 +303,8 @@ struct WsLayout {
 size_t layout(const Plan& p, void* base, WsLayout* out) {
     WsCarver w(base);
     WsLayout l{};
-    l.queue = w.take<unsigned int>(8);
-    if (p.algo == FT_ALGO_THREAD) l.ovf = w.take<uint32_t>(size_t(p.n_pairs));
+    l.queue = w.take<unsigned int>(4);
+    if (p.algo == FT_ALGO_THREAD) l.gres = w.take<uint32_t>(size_t(p.tblocks) * p.twarps * 32 * p.tmaxn);
     if (p.need_order) {
         l.order = w.take<uint32_t>(size_t(p.n_pairs));
         l.keys = w.take<uint32_t>(size_t(p.n_pairs));
@@ -343,7 +356,7 @@ FlowCtx make_ctx(const ft_tree* t, const float* vocab, const ft_docs* a, const f
 
 ft_status launch_warps(const Plan& p, const FlowCtx& c, bool save, cudaStream_t s) {
     const int64_t n_warps = int64_t(p.blocks) * p.warps;
-    int64_t grab = c.n_dev ? 1 : c.n_pairs / (n_warps * 32);
+    int64_t grab = c.n_pairs / (n_warps * 32);
     grab = std::max<int64_t>(1, std::min<int64_t>(grab, 16));
     void* fn = persistent_kernel(p.mode, save);
     FlowCtx cc = c;
@@ -354,20 +367,14 @@ ft_status launch_warps(const Plan& p, const FlowCtx& c, bool save, cudaStream_t 
 }
 
 ft_status launch_persistent(const Plan& p, const WsLayout& l, FlowCtx c, bool save, cudaStream_t s) {
-    FT_CUDA(cudaMemsetAsync(c.queue, 0, 32, s));
+    FT_CUDA(cudaMemsetAsync(c.queue, 0, 8, s));
     if (p.algo != FT_ALGO_THREAD) return launch_warps(p, c, save, s);
-    // lane per pair, then the warp kernel over the pairs it could not hold
     void* fn = thread_kernel(save);
-    int tcap = p.tcap, tbytes = p.tables_bytes;
-    uint32_t* ovf = l.ovf;
-    unsigned int* n_ovf = c.queue + 4;
-    void* args[] = {&c, &tcap, &tbytes, &ovf, &n_ovf};
+    int tw = p.tw, tbytes = p.tables_bytes, nmax = p.tmaxn;
+    uint32_t* gres = l.gres;
+    void* args[] = {&c, &tw, &tbytes, &gres, &nmax};
     FT_CUDA(cudaLaunchKernel(fn, dim3(p.tblocks), dim3(p.twarps * 32), args, p.tsmem, s));
-    FlowCtx c2 = c;
-    c2.queue = c.queue + 2;
-    c2.order = l.ovf;
-    c2.n_dev = c.queue + 4;
-    return launch_warps(p, c2, save, s);
+    return FT_OK;
 }
 
 ft_status run_batch(const ft_tree* t, const float* vocab, const ft_docs* a, const ft_docs* b, const int32_t* pa,
@@ -451,7 +458,7 @@ extern "C" size_t ft_flowtree_batch_workspace_size(const ft_tree* t, const ft_do
     Plan pt;
     ft_flowtree_config tc = t->cfg;
     tc.algo = FT_ALGO_THREAD;
-    tc.stage_items = 32;
+    tc.warps_per_cta = 1;
     if (t->dim <= 8 && make_plan(t, a, b, n_pairs, 0, false, true, tc, &pt) == FT_OK)
         need = std::max(need, layout(pt, nullptr, nullptr));
     return need;
@@ -515,8 +522,7 @@ extern "C" ft_status ft_flowtree_autotune(ft_tree* t, const float* vocab_dev, co
     }
     if (t->dim <= 8 && maxn <= kThreadMaxItems) {
         // lane per pair: warps per block x item buffer entries per lane
-        const int tc[][2] = {{3, 256}, {6, 128}};
-        for (const auto& x : tc) cands.push_back({x[0], x[1], FT_ALGO_THREAD, 0});
+        for (int w : {2, 4, 8}) cands.push_back({w, 0, FT_ALGO_THREAD, 0});
     }
     if (cands.empty()) cands.push_back({kDefaultWarps, std::min(maxn, 512), FT_ALGO_WARP, 0});
     cudaEvent_t e0, e1;

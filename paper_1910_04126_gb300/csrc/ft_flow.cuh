@@ -60,7 +60,6 @@ struct FlowCtx {
     int64_t na_docs;
     int64_t nb_docs;
     const uint32_t* order;  // NULL -> identity
-    const unsigned int* n_dev;  // non-NULL: the pair count, read on the device (n_pairs is then a bound)
     unsigned int* queue;
     float* cost_out;
     // saved flows (NULL = not saved)

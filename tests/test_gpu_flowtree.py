@@ -217,14 +217,13 @@ def test_rejects_bad_inputs():
 
 
 @pytest.mark.parametrize("name", ["grid", "tiny2d"])
-@pytest.mark.parametrize("cap", [32, 64])
-def test_thread_form_overflow_goes_to_warp_kernel(name, cap):
-    """Lane-per-pair form with item buffers too small for many pairs: those
-    pairs are finished by the warp-per-pair kernel; costs and saved flows stay
-    exact."""
+@pytest.mark.parametrize("warps", [1, 8])
+def test_thread_form_block_shapes(name, warps):
+    """Thread-per-pair form with one and eight warps per CTA (every lane takes
+    pairs from the shared queue): costs and saved flows exact."""
     pts, L, shift, db, q = CASES[name]
     tree, otree = build_both(pts, L, shift)
-    tree.set_config(2, cap, 2)
+    tree.set_config(warps, 0, 2)
     Dd, Dq = api.Docs.from_csr(tree, db), api.Docs.from_csr(tree, q)
     Sd, Sq = oracle_supports(otree, db), oracle_supports(otree, q)
     got = api.flowtree_batch(tree, tree.points, Dq, Dd).cpu().numpy().astype(np.float64)
