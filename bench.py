@@ -469,6 +469,10 @@ def extras(args, tree, D, Q, q_h, db_h, pts, shift, batched_value, dev, pk, pk_k
     tdb = synth.zipf_docs(nwt, ndb, 302)
     tq = synth.zipf_docs(nwt, nqt, 303)
     D3, Q3 = api.Docs.from_csr(t3, tdb), api.Docs.from_csr(t3, tq)
+    # launch configuration for these documents, tuned on a 2-query cross product
+    Qs3 = api.Docs.from_csr(t3, tq.subset(np.arange(2)))
+    tuned3 = api.flowtree_autotune(t3, t3.points, Qs3, D3)
+    del Qs3
     kws = torch.empty(api.knn_workspace_size(t3, D3, Q3, k1, TOPK), dtype=torch.uint8, device=dev)
     kid = torch.empty((nqt, TOPK), dtype=torch.int32, device=dev)
     kdist = torch.empty((nqt, TOPK), dtype=torch.float32, device=dev)
@@ -491,6 +495,7 @@ def extras(args, tree, D, Q, q_h, db_h, pts, shift, batched_value, dev, pk, pk_k
     out["text_knn_pipeline"] = {
         "flowtree_pairs_per_s": nqt * k1 / (ms3 * 1e-3), "queries_per_s": nqt / (ms3 * 1e-3),
         "scan_pairs_per_s": nqt * ndb / (ms3 * 1e-3), "batch_ms_median": ms3, "graph": True,
+        "launch_config": list(tuned3),
         "scan_roofline": scan_roofline(t3, Q3, D3, pk, pk_kind),
         "workload": "vocab %d x 300, %d docs (log-normal lengths, Zipf(1.1) words), %d queries, top-%d -> top-%d"
                     % (nwt, ndb, nqt, k1, TOPK)}

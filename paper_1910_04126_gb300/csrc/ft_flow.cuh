@@ -182,7 +182,8 @@ __device__ __forceinline__ float dist_group(const FlowCtx& c, uint32_t wa, uint3
         const float4* x = reinterpret_cast<const float4*>(c.vocab + size_t(wa) * c.dim);
         const float4* y = reinterpret_cast<const float4*>(c.vocab + size_t(wb) * c.dim);
         const int n4 = c.dim >> 2;
-        for (int t = int(sub); t < n4; t += 8) {
+#pragma unroll 4
+        for (int t = int(sub); t < n4; t += 8) {  // several row loads in flight
             const float4 p = __ldg(x + t), q = __ldg(y + t);
             const float d0 = p.x - q.x, d1 = p.y - q.y, d2 = p.z - q.z, d3 = p.w - q.w;
             s = fmaf(d0, d0, s);
@@ -193,6 +194,7 @@ __device__ __forceinline__ float dist_group(const FlowCtx& c, uint32_t wa, uint3
     } else {
         const float* x = c.vocab + size_t(wa) * c.dim;
         const float* y = c.vocab + size_t(wb) * c.dim;
+#pragma unroll 4
         for (int t = int(sub); t < c.dim; t += 8) {
             const float df = __ldg(x + t) - __ldg(y + t);
             s = fmaf(df, df, s);
