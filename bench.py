@@ -500,6 +500,29 @@ def extras(args, tree, D, Q, q_h, db_h, pts, shift, batched_value, dev, pk, pk_k
         "workload": "vocab %d x 300, %d docs (log-normal lengths, Zipf(1.1) words), %d queries, top-%d -> top-%d"
                     % (nwt, ndb, nqt, k1, TOPK)}
 
+    # the Mean method (centroid distance) as the first stage instead of the quadtree
+    try:
+        mws = torch.empty(api._ffi.load().ft_mean_scan_workspace_size(Q3.handle, D3.handle, k1), dtype=torch.uint8,
+                          device=dev)
+        api.mean_scan(t3, t3.points, Q3, D3, k1, workspace=mws)
+        torch.cuda.synchronize()
+        e0.record()
+        m_ids, _ = api.mean_scan(t3, t3.points, Q3, D3, k1, workspace=mws)
+        e1.record()
+        e1.synchronize()
+        mean_ms = e0.elapsed_time(e1)
+        del mws
+        q_ids = api.quadtree_scan(t3, Q3, D3, k1)
+        fin, mi, qi = kid.cpu().numpy(), m_ids.cpu().numpy(), q_ids.cpu().numpy()
+        out["text_mean_prefilter"] = {
+            "scan_ms": mean_ms, "pairs_per_s": nqt * ndb / (mean_ms * 1e-3), "k1": k1,
+            "flowtree_top10_within_mean_top_k1": float(np.mean([len(set(f) & set(m)) / TOPK for f, m in zip(fin, mi)])),
+            "flowtree_top10_within_quadtree_top_k1": float(np.mean([len(set(f) & set(q_)) / TOPK
+                                                                  for f, q_ in zip(fin, qi)])),
+            "stage": "centroid distances: FP32 centroids, cuBLAS SGEMM cross terms, top-k1 select (ft_mean_scan)"}
+    except Exception as ex:  # report, do not lose the main line
+        out["text_mean_prefilter"] = {"error": "%s: %s" % (type(ex).__name__, ex)}
+
     # three-stage pipeline: quadtree -> top-1,000 -> Flowtree -> top-20 -> exact W1 -> top-10
     try:
         nq_x = 100 if not args.quick else 20

@@ -335,6 +335,23 @@ ft_status ft_exact_w1_batch(const float* vocab_dev, const ft_docs* a, const ft_d
                             size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------
+ * Mean-distance prefilter (the "Mean" method of Sec. 5): for every query q
+ * and database document d, ||sum_i mu_q(i) x_i - sum_j mu_d(j) y_j||_2, the
+ * distance between the mass-weighted centroids over the rows of vocab_dev
+ * float32 [n_points][dim] (a lower bound on W1).  cand_ids_out_dev int32
+ * [nq][k1] / cand_dist_out_dev float32 [nq][k1]: the k1 smallest per query,
+ * ascending by (distance, document id).  FP32 throughout: the centroid cross
+ * products are one cuBLAS SGEMM (FP32 math mode), the distance
+ * sqrt(|c_q|^2 + |c_d|^2 - 2 c_q . c_d).  k1 <= min(n_db, 4096).
+ * Allocation-free; not for use inside stream capture (cuBLAS may pick a
+ * workspace of its own).
+ * ------------------------------------------------------------------------ */
+size_t ft_mean_scan_workspace_size(const ft_docs* queries, const ft_docs* db, int32_t k1);
+ft_status ft_mean_scan(const float* vocab_dev, const ft_docs* queries, const ft_docs* db, int32_t k1,
+                       void* workspace, size_t ws_bytes, int32_t* cand_ids_out_dev, float* cand_dist_out_dev,
+                       void* stream);
+
+/* ------------------------------------------------------------------------
  * Three-stage nearest-neighbour pipeline (Sec. 5.2; Flowtree as the
  * intermediate stage of Sec. 5.3's tuned pipelines): quadtree scan ->
  * top-k1 -> batched Flowtree -> top-k2 -> exact W1 -> top-k per query.

@@ -623,6 +623,20 @@ double oracle_exact_w1(const float* vocab, int32_t d, const int64_t* pa, const i
     return min_cost_flow(sup, dem, cost) / double(kMassOne);
 }
 
+// The "Mean" method of Sec. 5: the Euclidean distance between the two
+// mass-weighted centroids sum_i (m_i / 2^24) x_i, in FP64.
+double oracle_mean_distance(const float* vocab, int32_t d, const int64_t* pa, const int64_t* ma, int64_t na,
+                            const int64_t* pb, const int64_t* mb, int64_t nb) {
+    double sq = 0.0;
+    for (int32_t t = 0; t < d; ++t) {
+        double ca = 0.0, cb = 0.0;
+        for (int64_t i = 0; i < na; ++i) ca += double(ma[i]) / double(kMassOne) * double(vocab[size_t(pa[i]) * d + t]);
+        for (int64_t j = 0; j < nb; ++j) cb += double(mb[j]) / double(kMassOne) * double(vocab[size_t(pb[j]) * d + t]);
+        sq += (ca - cb) * (ca - cb);
+    }
+    return std::sqrt(sq);
+}
+
 // Exact W1 under the quadtree metric t (units of u * 2^-24), by the same
 // min-cost flow solver: an independent check of the closed form.
 double oracle_tree_w1_mcf(void* h, const int64_t* pa, const int64_t* ma, int64_t na, const int64_t* pb,

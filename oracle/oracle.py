@@ -17,6 +17,7 @@ __all__ = [
     "OracleTree",
     "Supports",
     "exact_w1",
+    "mean_distance",
     "min_cost_flow",
     "topk_ids",
     "MASS_ONE",
@@ -71,6 +72,7 @@ def load():
     _sig(lib.oracle_flowtree_grad_batch, None, vp, _f32p, _i64p, _i64p, _i64p, _i64p, _i64p, _i64p,
          _i64p, _i64p, _f64p, C.c_int64, _f64p)
     _sig(lib.oracle_exact_w1, C.c_double, _f32p, C.c_int32, _i64p, _i64p, C.c_int64, _i64p, _i64p, C.c_int64)
+    _sig(lib.oracle_mean_distance, C.c_double, _f32p, C.c_int32, _i64p, _i64p, C.c_int64, _i64p, _i64p, C.c_int64)
     _sig(lib.oracle_tree_w1_mcf, C.c_double, vp, _i64p, _i64p, C.c_int64, _i64p, _i64p, C.c_int64)
     _sig(lib.oracle_min_cost_flow, C.c_double, _i64p, C.c_int64, _i64p, C.c_int64, _f64p)
     _lib = lib
@@ -242,6 +244,15 @@ def exact_w1(vocab, pa, ma, pb, mb) -> float:
     pa, ma, pb, mb = map(_i64, (pa, ma, pb, mb))
     return float(lib.oracle_exact_w1(_p(vocab, _f32p), vocab.shape[1], _p(pa, _i64p), _p(ma, _i64p), len(pa),
                                      _p(pb, _i64p), _p(mb, _i64p), len(pb)))
+
+
+def mean_distance(vocab, pa, ma, pb, mb) -> float:
+    """The Mean method (Sec. 5): distance between the mass-weighted centroids."""
+    lib = load()
+    vocab = np.ascontiguousarray(vocab, dtype=np.float32)
+    pa, ma, pb, mb = map(_i64, (pa, ma, pb, mb))
+    return float(lib.oracle_mean_distance(_p(vocab, _f32p), vocab.shape[1], _p(pa, _i64p), _p(ma, _i64p), len(pa),
+                                          _p(pb, _i64p), _p(mb, _i64p), len(pb)))
 
 
 def min_cost_flow(supply, demand, cost) -> float:

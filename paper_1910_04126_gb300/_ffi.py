@@ -74,6 +74,8 @@ SIGNATURES = {
     "ft_quadtree_scan_matches": (i32, [vp, vp, vp, C.POINTER(i64)]),
     "ft_knn_workspace_size": (sz, [vp, vp, vp, i32, i32]),
     "ft_knn": (i32, [vp, vp, vp, vp, i32, i32, vp, sz, vp, vp, vp]),
+    "ft_mean_scan_workspace_size": (sz, [vp, vp, i32]),
+    "ft_mean_scan": (i32, [vp, vp, vp, i32, vp, sz, vp, vp, vp]),
     "ft_exact_w1_workspace_size": (sz, [vp, vp, i64]),
     "ft_exact_w1_batch": (i32, [vp, vp, vp, vp, vp, i64, vp, vp, sz, vp]),
     "ft_knn_exact_workspace_size": (sz, [vp, vp, vp, i32, i32, i32]),

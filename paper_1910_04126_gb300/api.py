@@ -340,6 +340,20 @@ def knn(tree: Tree, vocab: torch.Tensor, db: Docs, queries: Docs, k1: int, k: in
     return ids, dist
 
 
+def mean_scan(tree: Tree, vocab: torch.Tensor, queries: Docs, db: Docs, k1: int,
+              workspace: Optional[torch.Tensor] = None, stream=None):
+    """k1 nearest database documents per query by centroid distance (ft_mean_scan): (ids, distances)."""
+    lib = _ffi.load()
+    nq = queries.n_docs
+    ids = torch.empty((nq, k1), dtype=torch.int32, device=tree.device)
+    dist = torch.empty((nq, k1), dtype=torch.float32, device=tree.device)
+    ws = _workspace(lib.ft_mean_scan_workspace_size(queries.handle, db.handle, k1), tree.device, workspace)
+    code = lib.ft_mean_scan(_ptr(vocab), queries.handle, db.handle, k1, _ptr(ws), ws.numel(), _ptr(ids), _ptr(dist),
+                            _stream(stream))
+    check(code, "ft_mean_scan")
+    return ids, dist
+
+
 def exact_w1_workspace_size(a: Docs, b: Docs, n_pairs: int) -> int:
     return int(_ffi.load().ft_exact_w1_workspace_size(a.handle, b.handle, n_pairs))
 

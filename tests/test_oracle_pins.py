@@ -448,3 +448,34 @@ def test_batch_entry_points_agree_with_single_calls():
 def test_topk_ties_by_smaller_id():
     v = np.array([3.0, 1.0, 2.0, 1.0, 0.5])
     assert O.topk_ids(v, 3).tolist() == [4, 1, 3]
+
+
+# ---------------------------------------------------------------------------
+# the Mean method (Sec. 5): centroid distance, a lower bound on W1
+# ---------------------------------------------------------------------------
+
+def test_mean_distance_pins():
+    rng = np.random.default_rng(31)
+    X = rng.random((40, 3)).astype(np.float32)
+    # Dirac against Dirac: the distance of the two points
+    d = O.mean_distance(X, [3], [ONE], [17], [ONE])
+    assert d == pytest.approx(np.linalg.norm(X[3].astype(np.float64) - X[17]), rel=1e-12)
+    # a distribution against itself: 0
+    m = np.array([ONE // 4, ONE // 4, ONE // 2])
+    assert O.mean_distance(X, [1, 2, 5], m, [1, 2, 5], m) == 0.0
+    # the centroid of two equal masses is the midpoint: distance to the midpoint's Dirac-like pair
+    half = [ONE // 2, ONE // 2]
+    mid = (X[4].astype(np.float64) + X[9]) / 2
+    assert O.mean_distance(X, [4, 9], half, [11], [ONE]) == pytest.approx(np.linalg.norm(mid - X[11]), rel=1e-12)
+    # Jensen: never above exact W1, on random distributions
+    for t in range(20):
+        na, nb = rng.integers(1, 7), rng.integers(1, 7)
+        pa = rng.choice(40, na, replace=False)
+        pb = rng.choice(40, nb, replace=False)
+        ma = rng.integers(1, 100, na)
+        mb = rng.integers(1, 100, nb)
+        ma = ma * ONE // ma.sum()
+        ma[0] += ONE - ma.sum()
+        mb = mb * ONE // mb.sum()
+        mb[0] += ONE - mb.sum()
+        assert O.mean_distance(X, pa, ma, pb, mb) <= O.exact_w1(X, pa, ma, pb, mb) * (1 + 1e-12) + 1e-15
