@@ -513,12 +513,20 @@ def extras(args, tree, D, Q, q_h, db_h, pts, shift, batched_value, dev, pk, pk_k
         mean_ms = e0.elapsed_time(e1)
         del mws
         q_ids = api.quadtree_scan(t3, Q3, D3, k1)
-        fin, mi, qi = kid.cpu().numpy(), m_ids.cpu().numpy(), q_ids.cpu().numpy()
+        # exhaustive Flowtree top-10 of the first queries: how much of it each first stage keeps
+        nx = min(50, nqt)
+        Qx = api.Docs.from_csr(t3, tq.subset(np.arange(nx)))
+        costs = api.flowtree_batch(t3, t3.points, Qx, D3)
+        ex_ids, _ = api.topk_f32(costs.view(nx, ndb), TOPK)
+        del costs
+        ex, mi, qi = ex_ids.cpu().numpy(), m_ids[:nx].cpu().numpy(), q_ids[:nx].cpu().numpy()
         out["text_mean_prefilter"] = {
             "scan_ms": mean_ms, "pairs_per_s": nqt * ndb / (mean_ms * 1e-3), "k1": k1,
-            "flowtree_top10_within_mean_top_k1": float(np.mean([len(set(f) & set(m)) / TOPK for f, m in zip(fin, mi)])),
-            "flowtree_top10_within_quadtree_top_k1": float(np.mean([len(set(f) & set(q_)) / TOPK
-                                                                  for f, q_ in zip(fin, qi)])),
+            "exhaustive_flowtree_top10_kept_by_mean_top_k1": float(np.mean([len(set(e) & set(m)) / TOPK
+                                                                          for e, m in zip(ex, mi)])),
+            "exhaustive_flowtree_top10_kept_by_quadtree_top_k1": float(np.mean([len(set(e) & set(q_)) / TOPK
+                                                                              for e, q_ in zip(ex, qi)])),
+            "queries_checked": nx,
             "stage": "centroid distances: FP32 centroids, cuBLAS SGEMM cross terms, top-k1 select (ft_mean_scan)"}
     except Exception as ex:  # report, do not lose the main line
         out["text_mean_prefilter"] = {"error": "%s: %s" % (type(ex).__name__, ex)}

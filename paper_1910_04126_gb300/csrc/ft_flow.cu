@@ -271,7 +271,10 @@ ft_status make_plan(const ft_tree* t, const ft_docs* a, const ft_docs* b, int64_
         int bps = 0;
         FT_TRY(ft_prepare_kernel(thread_kernel(save), p->twarps * 32, p->tsmem, &bps));
         if (bps < 1) return FT_EUNSUPPORTED;
-        p->tblocks = sms * bps;
+        // resident blocks, but no more threads than pairs (each thread owns a
+        // slice of residual words in the workspace)
+        const int64_t need_blocks = (std::max<int64_t>(n_pairs, 1) + p->twarps * 32 - 1) / (p->twarps * 32);
+        p->tblocks = int(std::min<int64_t>(int64_t(sms) * bps, need_blocks));
         return FT_OK;
     }
     int cap = wcfg.stage_items > 0 ? round32(wcfg.stage_items) : std::min(maxn, 512);
@@ -452,16 +455,7 @@ extern "C" size_t ft_flowtree_batch_workspace_size(const ft_tree* t, const ft_do
     if (t->dim > 8 && make_plan(t, a, b, n_pairs, 1, false, true, t->cfg, &p1) != FT_OK) return 0;
     Plan p2 = p;
     if (t->dim > 8 && make_plan(t, a, b, n_pairs, 2, true, true, t->cfg, &p2) != FT_OK) return 0;
-    size_t need = std::max(layout(p, nullptr, nullptr), std::max(layout(p1, nullptr, nullptr), layout(p2, nullptr, nullptr)));
-    // room for the lane-per-pair form too, so that a workspace sized before
-    // ft_flowtree_autotune fits whatever it picks
-    Plan pt;
-    ft_flowtree_config tc = t->cfg;
-    tc.algo = FT_ALGO_THREAD;
-    tc.warps_per_cta = 1;
-    if (t->dim <= 8 && make_plan(t, a, b, n_pairs, 0, false, true, tc, &pt) == FT_OK)
-        need = std::max(need, layout(pt, nullptr, nullptr));
-    return need;
+    return std::max(layout(p, nullptr, nullptr), std::max(layout(p1, nullptr, nullptr), layout(p2, nullptr, nullptr)));
 }
 
 extern "C" ft_status ft_flowtree_batch(const ft_tree* t, const float* vocab_dev, const ft_docs* a, const ft_docs* b,
