@@ -177,27 +177,26 @@ __device__ float exact_pair(const ExactCtx& c, int64_t da, int64_t db, float* cm
             const float pu = pi[u];
             if (u < na) {  // forward arcs u -> every demand node
                 const float* row = cm + size_t(u) * nb;
-                int j = int(lane);
-                for (; j + 32 < nb; j += 64) {  // two rows entries, their loads in flight together
-                    const float c0 = row[j], c1 = row[j + 32];
-                    const float q0 = pi[na + j], q1 = pi[na + j + 32];
-                    const float e0 = dist[na + j], e1 = dist[na + j + 32];
-                    const float n0 = best + fmaxf(0.0f, c0 + pu - q0), n1 = best + fmaxf(0.0f, c1 + pu - q1);
-                    if (!settled(e0) && n0 < e0) {
-                        dist[na + j] = n0;
-                        pred[na + j] = int16_t(u);
+                // eight row entries per lane loaded before any store, so that
+                // their (L2) latencies overlap
+                for (int j0 = int(lane); j0 < nb; j0 += 32 * 8) {
+                    float cv[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const int j = j0 + 32 * k;
+                        cv[k] = j < nb ? row[j] : 0.0f;
                     }
-                    if (!settled(e1) && n1 < e1) {
-                        dist[na + j + 32] = n1;
-                        pred[na + j + 32] = int16_t(u);
-                    }
-                }
-                for (; j < nb; j += 32) {
-                    const float e0 = dist[na + j];
-                    const float n0 = best + fmaxf(0.0f, row[j] + pu - pi[na + j]);
-                    if (!settled(e0) && n0 < e0) {
-                        dist[na + j] = n0;
-                        pred[na + j] = int16_t(u);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const int j = j0 + 32 * k;
+                        if (j < nb) {
+                            const float e0 = dist[na + j];
+                            const float n0 = best + fmaxf(0.0f, cv[k] + pu - pi[na + j]);
+                            if (!settled(e0) && n0 < e0) {
+                                dist[na + j] = n0;
+                                pred[na + j] = int16_t(u);
+                            }
+                        }
                     }
                 }
             } else {  // backward arcs: demand node u -> supply nodes that ship to it (bitmap)
@@ -281,7 +280,7 @@ __device__ float exact_pair(const ExactCtx& c, int64_t da, int64_t db, float* cm
     return float(acc / 16777216.0);
 }
 
-__global__ void __launch_bounds__(EX_WARPS * 32) k_exact_w1(ExactCtx c) {
+__global__ void __launch_bounds__(EX_WARPS * 32, 4) k_exact_w1(ExactCtx c) {
     extern __shared__ __align__(16) uint8_t smem[];
     const int warp = int(threadIdx.x >> 5);
     const unsigned lane = lane_id();
