@@ -70,6 +70,9 @@ def parse():
     ap.add_argument("--profile-scan", nargs=2, type=int, metavar=("N_DB", "N_Q"),
                     help="only run the quadtree scan + top-1,000 of N_Q text-shaped queries over N_DB documents "
                          "(vocabulary 100,000 x 300) three times (a case for ncu); no timing")
+    ap.add_argument("--profile-exact", nargs=2, type=int, metavar=("N_Q", "PER_Q"),
+                    help="only run exact W1 on N_Q text-shaped queries x PER_Q random documents of 20,000 "
+                         "(vocabulary 100,000 x 300) three times (a case for ncu); no timing")
     return ap.parse_args()
 
 
@@ -105,6 +108,25 @@ def profile_scan(args):
     torch.cuda.synchronize()
     print("profile scan done: %d x %d, %d db embedding entries, status %d"
           % (n_q, n_db, D.info.n_embed, tree.status()))
+
+
+def profile_exact(args):
+    import torch
+    from paper_1910_04126_gb300 import api, synth
+    n_q, per_q = args.profile_exact
+    vocab = synth.mixture_vocab(100000, 300, 1000, 0.3, 300)
+    db = synth.zipf_docs(100000, 20000, 302)
+    q = synth.zipf_docs(100000, n_q, 303)
+    tree = api.Tree(torch.as_tensor(vocab, device="cuda"), LEVELS, synth.random_shift(300, 301))
+    D, Q = api.Docs.from_csr(tree, db), api.Docs.from_csr(tree, q)
+    rng = np.random.default_rng(0)
+    pa = torch.as_tensor(np.repeat(np.arange(n_q), per_q), dtype=torch.int32, device="cuda")
+    pb = torch.as_tensor(rng.integers(0, db.n, n_q * per_q), dtype=torch.int32, device="cuda")
+    ws = torch.empty(api.exact_w1_workspace_size(Q, D, n_q * per_q), dtype=torch.uint8, device="cuda")
+    for _ in range(3):
+        api.exact_w1(tree, tree.points, Q, D, pa, pb, workspace=ws)
+    torch.cuda.synchronize()
+    print("profile exact done: %d pairs, status %d" % (n_q * per_q, tree.status()))
 
 
 # ---------------------------------------------------------------------------
@@ -260,6 +282,9 @@ def main():
         return
     if args.profile_scan:
         profile_scan(args)
+        return
+    if args.profile_exact:
+        profile_exact(args)
         return
 
     import torch

@@ -255,14 +255,14 @@ def flowtree_autotune(tree: Tree, vocab: torch.Tensor, a: Docs, b: Docs, pair_a=
     # the largest candidate staging needs the most workspace: size for it
     saved = tree.get_config()
     best_ws = 0
-    for w in (2, 3, 4, 5, 6, 7, 8):
-        for cap in (32, 256, 384, 512, 768, 1024):
-            try:
-                tree.set_config(w, cap, _ffi.ALGO_WARP)
-                best_ws = max(best_ws, lib.ft_flowtree_batch_workspace_size(tree.handle, a.handle, b.handle,
-                                                                             n_pairs))
-            except _ffi.FlowtreeError:
-                pass
+    shapes = [(w, cap, _ffi.ALGO_WARP) for w in (2, 3, 4, 5, 6, 7, 8) for cap in (32, 256, 384, 512, 768, 1024)]
+    shapes += [(w, 0, _ffi.ALGO_THREAD) for w in (2, 4, 8)]
+    for w, cap, algo in shapes:
+        try:
+            tree.set_config(w, cap, algo)
+            best_ws = max(best_ws, lib.ft_flowtree_batch_workspace_size(tree.handle, a.handle, b.handle, n_pairs))
+        except _ffi.FlowtreeError:
+            pass
     tree.set_config(*saved)
     ws = _workspace(best_ws, tree.device, None)
     cfg = _ffi.FlowtreeConfig()
