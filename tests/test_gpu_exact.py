@@ -118,3 +118,27 @@ def test_knn_exact_graph_capture_replay():
     g.replay()
     torch.cuda.synchronize()
     assert torch.equal(ids, ref_ids) and torch.equal(dist, ref_dist)
+
+
+def test_exact_and_pipeline_reject_bad_inputs():
+    pts, L, shift, db, q, _ = CASES["tiny2d"]
+    tree = api.Tree(torch.as_tensor(pts, device="cuda"), L, shift)
+    Dd, Dq = api.Docs.from_csr(tree, db), api.Docs.from_csr(tree, q)
+    # a pair index out of range: NaN for that pair, FT_EINVAL in the status word, the others exact
+    pa = np.array([0, 1, q.n + 5])
+    pb = np.array([3, 4, 0])
+    got = api.exact_w1(tree, tree.points, Dq, Dd, pa, pb).cpu().numpy()
+    assert np.isnan(got[2]) and np.all(np.isfinite(got[:2]))
+    assert tree.status() == -1
+    assert tree.status() == 0  # read and cleared
+    # stage sizes out of order, and documents of another tree
+    with pytest.raises(api._ffi.FlowtreeError):
+        api.knn_exact(tree, tree.points, Dd, Dq, 20, 30, 5)
+    with pytest.raises(api._ffi.FlowtreeError):
+        api.knn_exact(tree, tree.points, Dd, Dq, 20, 10, 11)
+    other = api.Tree(torch.as_tensor(pts, device="cuda"), L, shift)
+    Do = api.Docs.from_csr(other, db)
+    with pytest.raises(api._ffi.FlowtreeError):
+        api.exact_w1(tree, tree.points, Dq, Do, [0], [0])
+    with pytest.raises(api._ffi.FlowtreeError):
+        api.mean_scan(tree, tree.points, Dq, Dd, db.n + 1)
