@@ -32,7 +32,7 @@ namespace {
 #define FT_SCAN_UNROLL 4   // warp loads of 32 postings in flight per step
 #endif
 constexpr int SCAN_THREADS = FT_SCAN_THREADS;
-constexpr int SEL_THREADS = 1024;
+constexpr int SEL_THREADS = 512;  // two CTAs per SM: a 256-row select fits one wave
 constexpr int MAX_K1 = 4096;
 
 // edge weight carried by an embedding entry
@@ -276,9 +276,21 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_u64(const uint64_t* __re
         for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
         __syncthreads();
         const uint64_t prefix = prefix_s, mask = mask_s;
-        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-            const uint64_t key = row[i];
-            if ((key & mask) == prefix) atomicAdd(&hist[(key >> (8 * dg)) & 255u], 1u);
+        // eight independent key loads in flight per thread (the row streams
+        // from L2/HBM once per digit)
+        const int64_t step = int64_t(blockDim.x) * 8;
+        for (int64_t i0 = threadIdx.x; i0 < n; i0 += step) {
+            uint64_t kv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int64_t i = i0 + int64_t(u) * blockDim.x;
+                kv[u] = i < n ? row[i] : ~uint64_t(0);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int64_t i = i0 + int64_t(u) * blockDim.x;
+                if (i < n && (kv[u] & mask) == prefix) atomicAdd(&hist[(kv[u] >> (8 * dg)) & 255u], 1u);
+            }
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -299,11 +311,19 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_u64(const uint64_t* __re
         __syncthreads();
     }
     const uint64_t thr = prefix_s;  // the k-th smallest key
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-        const uint64_t key = row[i];
-        if (key <= thr) {
-            const int pos = atomicAdd(&cnt_s, 1);
-            if (pos < MAX_K1) cand[pos] = key;
+    for (int64_t i0 = threadIdx.x; i0 < n; i0 += int64_t(blockDim.x) * 8) {
+        uint64_t kv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int64_t i = i0 + int64_t(u) * blockDim.x;
+            kv[u] = i < n ? row[i] : ~uint64_t(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (kv[u] <= thr && i0 + int64_t(u) * blockDim.x < n) {
+                const int pos = atomicAdd(&cnt_s, 1);
+                if (pos < MAX_K1) cand[pos] = kv[u];
+            }
         }
     }
     __syncthreads();
