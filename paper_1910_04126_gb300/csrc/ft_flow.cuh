@@ -241,14 +241,19 @@ __device__ __forceinline__ void price_queue(const FlowCtx& c, const WarpBuf& w, 
         }
     } else {
         const unsigned grp = lane >> 3, sub = lane & 7u;
+        // the words of all queued pairs at once, one pair per lane, so that the
+        // rounds below wait on row loads only
+        uint32_t my_wa = 0, my_wb = 0;
+        if (int(lane) < cnt) {
+            const uint32_t q = w.qe[lane];
+            my_wa = __ldg(c.a_word + ao + (q & 0xFFFFu));
+            my_wb = __ldg(c.b_word + bo + (q >> 16));
+        }
         for (int r0 = 0; r0 < cnt; r0 += 4) {
             const int e = r0 + int(grp);
-            uint32_t wa = 0, wb = 0;  // idle group: a zero-length pair (row 0 twice)
-            if (e < cnt) {
-                const uint32_t q = w.qe[e];
-                wa = __ldg(c.a_word + ao + (q & 0xFFFFu));
-                wb = __ldg(c.b_word + bo + (q >> 16));
-            }
+            uint32_t wa = __shfl_sync(FULL_MASK, my_wa, e & 31);
+            uint32_t wb = __shfl_sync(FULL_MASK, my_wb, e & 31);
+            if (e >= cnt) wa = wb = 0;  // idle group: a zero-length pair (row 0 twice)
             // every lane takes part: dist_group shuffles across the warp
             const float dist = dist_group<MODE>(c, wa, wb, sub);
             if (e < cnt && sub == 0) {
