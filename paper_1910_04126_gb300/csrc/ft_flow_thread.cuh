@@ -80,7 +80,6 @@ struct LanePair {
         const int nu_before = int(S(pcw, w)) + __popc(S(sidew, w) & ((1u << (x & 31)) - 1u));
         return s ? nu_before : x - nu_before;
     }
-    __device__ __forceinline__ bool used(int x) { return (S(usedw, x >> 5) >> (x & 31)) & 1u; }
     __device__ __forceinline__ void set_used(int x) { S(usedw, x >> 5) |= 1u << (x & 31); }
     // first position >= x that is not fully matched, or end
     __device__ __forceinline__ int next_live(int x, int end) {
@@ -146,8 +145,8 @@ struct LaneSweep {
     uint32_t ra = 0, rb = 0, prev = 0;
     int p = 0, nf = 0;
     // pending item
-    unsigned ps = 0;
-    int pidx = 0, pg = 0;
+    unsigned ps = 0;  // its side
+    int pg = 0;       // its gap: LCA depth with the previous item (-1 for the first)
     // current match: left front (pl, end le), right front (pr, end re)
     int mk = 0, pl = 0, le = 0, pr = 0, re = 0;
     unsigned sl = 0, sr = 0;
@@ -267,12 +266,12 @@ struct LaneSweep {
                 if (ia < P.na && (ib >= P.nb || ra <= rb)) {
                     r = ra;
                     ps = 0;
-                    pidx = ia++;
+                    ++ia;
                     ra = ia < P.na ? c.a_rank[P.ao + ia] : 0xFFFFFFFFu;
                 } else {
                     r = rb;
                     ps = 1;
-                    pidx = ib++;
+                    ++ib;
                     rb = ib < P.nb ? c.b_rank[P.bo + ib] : 0xFFFFFFFFu;
                 }
                 pg = p == 0 ? -1 : (r == prev ? P.L + 1 : lca_ranks(P.tb, c.n_points, prev, r));
