@@ -259,7 +259,6 @@ ft_status make_plan(const ft_tree* t, const ft_docs* a, const ft_docs* b, int64_
     FT_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     FT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     p->tables_bytes = cfg.stage_tables ? staged_tables_bytes(t) : 0;
-    ft_flowtree_config wcfg = cfg;
     if (p->algo == FT_ALGO_THREAD) {
         if (!thread_ok) return FT_EUNSUPPORTED;
         p->tw = (maxn + 31) / 32;
@@ -277,7 +276,7 @@ ft_status make_plan(const ft_tree* t, const ft_docs* a, const ft_docs* b, int64_
         p->tblocks = int(std::min<int64_t>(int64_t(sms) * bps, need_blocks));
         return FT_OK;
     }
-    int cap = wcfg.stage_items > 0 ? round32(wcfg.stage_items) : std::min(maxn, 512);
+    int cap = cfg.stage_items > 0 ? round32(cfg.stage_items) : std::min(maxn, 512);
     cap = std::min(cap, kMaxStage);
     p->cap = cap;
     p->smem = size_t(p->tables_bytes) + size_t(p->warps) * warpbuf_bytes(cap);
