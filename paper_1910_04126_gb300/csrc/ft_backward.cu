@@ -9,16 +9,55 @@
 //   1. one coefficient per saved flow record, two contributions per record
 //      (one per endpoint), keyed by the point they update;
 //   2. stable radix sort of the contributions by point;
-//   3. chunks of 32 sorted contributions -> one partial vector per run of
-//      equal points inside a chunk;
-//   4. per point, its partials (contiguous, in sorted order) are summed in
-//      order and added to grad.
+//   3. a warp per chunk of CHUNK sorted contributions sums every run of
+//      equal points in order.  A run that lies inside the chunk holds all of
+//      its point's contributions: the warp adds it to grad directly.  A run
+//      cut by a chunk boundary goes to one of the chunk's two partial slots
+//      (A: the run that continues from the previous chunk, B: the run that
+//      starts in this chunk and continues into the next);
+//   4. every B slot starts a chain B(c), A(c+1), A(c+2), ... of one point;
+//      a CTA per chain sums it in a fixed order (warp r takes elements r,
+//      r + 8, ...; the eight warp sums are then added in warp order) and adds
+//      the total to grad.
+// Rows are read as float4 when the dimension and the pointers allow it.
+#include <algorithm>
+#include <cstdint>
+
 #include "ft_internal.cuh"
 
 namespace {
 
-constexpr int CHUNK = 32;
-constexpr int COORD_BLOCK = 256;  // coordinates per pass: 8 per lane
+constexpr int CHUNK = 64;       // sorted contributions per warp
+constexpr int COLS = 3;         // row vectors per lane in one column block (block = 96 vectors)
+constexpr int CHAIN_WARPS = 8;  // warps per chain CTA
+
+__device__ __forceinline__ void vzero(float& a) { a = 0.0f; }
+__device__ __forceinline__ void vzero(float4& a) { a = make_float4(0.0f, 0.0f, 0.0f, 0.0f); }
+__device__ __forceinline__ void vfma_diff(float& a, float c, float x, float y) { a = fmaf(c, x - y, a); }
+__device__ __forceinline__ void vfma_diff(float4& a, float c, const float4& x, const float4& y) {
+    a.x = fmaf(c, x.x - y.x, a.x);
+    a.y = fmaf(c, x.y - y.y, a.y);
+    a.z = fmaf(c, x.z - y.z, a.z);
+    a.w = fmaf(c, x.w - y.w, a.w);
+}
+__device__ __forceinline__ void vadd(float& a, float b) { a += b; }
+__device__ __forceinline__ void vadd(float4& a, const float4& b) {
+    a.x += b.x;
+    a.y += b.y;
+    a.z += b.z;
+    a.w += b.w;
+}
+
+template <int VEC>
+struct VecOf;
+template <>
+struct VecOf<1> {
+    using T = float;
+};
+template <>
+struct VecOf<4> {
+    using T = float4;
+};
 
 __global__ void k_bwd_slots(const int64_t* __restrict__ slot_ptr, const int32_t* __restrict__ count,
                             const uint32_t* __restrict__ f_ia, const uint32_t* __restrict__ f_ib,
@@ -65,91 +104,212 @@ __global__ void k_bwd_slots(const int64_t* __restrict__ slot_ptr, const int32_t*
     }
 }
 
-// runs of equal non-sentinel keys inside each chunk of 32 sorted entries
-__global__ void k_bwd_chunk_runs(const uint32_t* __restrict__ key, const uint32_t* __restrict__ perm, int64_t n,
-                                 uint32_t sentinel, int64_t n_chunks, int64_t* __restrict__ runs) {
-    for (int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; c < n_chunks; c += int64_t(gridDim.x) * blockDim.x) {
-        int64_t r = 0;
-        uint32_t prev = sentinel;
-        const int64_t e1 = min(n, (c + 1) * CHUNK);
-        for (int64_t j = c * CHUNK; j < e1; ++j) {
-            const uint32_t k = key[perm[j]];
-            if (k != sentinel && (j == c * CHUNK || k != prev)) ++r;
-            prev = k;
+// A chunk of sorted contributions: its range, the keys just outside it and
+// the points that went to its two partial slots (sentinel = unused).
+struct RunChunk {
+    int64_t c, j0, j1;
+    uint32_t k_before, k_after, sentinel;
+    uint32_t used_a, used_b;
+};
+
+// Adds the run [rs, re) of point cur (column block cb) to grad when the run
+// holds all of the point's contributions, else to the chunk's partial slot
+// (A when it continues from the previous chunk, B when it continues into the
+// next one); clears the accumulators.
+template <class V>
+__device__ __forceinline__ void flush_run(V (&acc)[COLS], uint32_t cur, int64_t rs, int64_t re, RunChunk& rc, int cb,
+                                          int nv, unsigned lane, V* __restrict__ gv, V* __restrict__ pv) {
+    if (cur == rc.sentinel) return;
+    const bool from_prev = rs == rc.j0 && rc.k_before == cur;
+    const bool to_next = re == rc.j1 && rc.k_after == cur;
+    if (!from_prev && !to_next) {
+#pragma unroll
+        for (int t = 0; t < COLS; ++t) {
+            const int x = cb + t * 32 + int(lane);
+            if (x < nv) {
+                V g = gv[size_t(cur) * nv + x];
+                vadd(g, acc[t]);
+                gv[size_t(cur) * nv + x] = g;
+            }
         }
-        runs[c] = r;
+    } else {
+        const int64_t slot = 2 * rc.c + (from_prev ? 0 : 1);
+#pragma unroll
+        for (int t = 0; t < COLS; ++t) {
+            const int x = cb + t * 32 + int(lane);
+            if (x < nv) pv[size_t(slot) * nv + x] = acc[t];
+        }
+        if (from_prev) rc.used_a = cur; else rc.used_b = cur;
     }
+#pragma unroll
+    for (int t = 0; t < COLS; ++t) vzero(acc[t]);
 }
 
-__global__ void k_bwd_partials(const uint32_t* __restrict__ key, const uint32_t* __restrict__ perm, int64_t n,
-                               uint32_t sentinel, int64_t n_chunks, const int64_t* __restrict__ run_off,
-                               const uint32_t* __restrict__ s_wa, const uint32_t* __restrict__ s_wb,
-                               const float* __restrict__ s_coef, const float* __restrict__ vocab, int dim,
-                               uint32_t* __restrict__ part_word, float* __restrict__ part) {
+// Step 3: one warp per chunk of CHUNK sorted contributions.  Lane q of a
+// 32-entry window holds contribution q (its point, both rows and the signed
+// coefficient); the warp walks the window in order, two contributions at a
+// time so that four row loads per column are in flight.
+template <int VEC>
+__global__ void __launch_bounds__(256) k_bwd_runs(const uint32_t* __restrict__ key, const uint32_t* __restrict__ perm,
+                                                  int64_t n, uint32_t sentinel, const uint32_t* __restrict__ s_wa,
+                                                  const uint32_t* __restrict__ s_wb, const float* __restrict__ s_coef,
+                                                  const float* __restrict__ vocab, int dim, float* __restrict__ grad,
+                                                  uint32_t* __restrict__ part_word, float* __restrict__ part,
+                                                  uint32_t* __restrict__ heads, uint32_t* __restrict__ n_heads) {
+    using V = typename VecOf<VEC>::T;
+    const int nv = dim / VEC;  // vectors per row
+    const int64_t n_chunks = (n + CHUNK - 1) / CHUNK;
     const int64_t warps = int64_t(gridDim.x) * (blockDim.x / 32);
     const unsigned lane = lane_id();
+    const V* vv = reinterpret_cast<const V*>(vocab);
+    V* gv = reinterpret_cast<V*>(grad);
+    V* pv = reinterpret_cast<V*>(part);
     for (int64_t c = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) / 32; c < n_chunks; c += warps) {
-        const int64_t j = c * CHUNK + lane;
-        const uint32_t e = j < n ? perm[j] : 0u;
-        const uint32_t k = j < n ? key[e] : sentinel;
-        for (int cb = 0; cb < dim; cb += COORD_BLOCK) {
-            float acc[COORD_BLOCK / 32];
+        const int64_t j0 = c * CHUNK, j1 = min(n, j0 + CHUNK);
+        const uint32_t k_before = j0 > 0 ? key[perm[j0 - 1]] : sentinel;
+        const uint32_t k_after = j1 < n ? key[perm[j1]] : sentinel;
+        RunChunk rc{c, j0, j1, k_before, k_after, sentinel, sentinel, sentinel};
+        for (int cb = 0; cb < nv; cb += 32 * COLS) {
+            V acc[COLS];
 #pragma unroll
-            for (int t = 0; t < COORD_BLOCK / 32; ++t) acc[t] = 0.0f;
-            int64_t slot = run_off[c] - 1;
-            uint32_t prev = sentinel;
-            for (int q = 0; q < CHUNK; ++q) {
-                const uint32_t kq = __shfl_sync(FULL_MASK, k, q);
-                if (kq == sentinel) break;
-                const uint32_t eq = __shfl_sync(FULL_MASK, e, q);
-                if (q == 0 || kq != prev) {
-                    if (slot >= run_off[c]) {
+            for (int t = 0; t < COLS; ++t) vzero(acc[t]);
+            uint32_t cur = sentinel;  // point of the open run
+            int64_t rs = j0;          // where it started
+            int64_t end = j1;  // first sentinel (sentinels sort last)
+            for (int64_t jb = j0; jb < end; jb += 32) {
+                const int64_t j = jb + lane;
+                uint32_t k = sentinel, wa = 0, wb = 0;
+                float cf = 0.0f;
+                if (j < end) {
+                    const uint32_t e = perm[j];
+                    k = key[e];
+                    if (k != sentinel) {
+                        const uint32_t s = e >> 1;
+                        wa = s_wa[s];
+                        wb = s_wb[s];
+                        cf = (e & 1u) ? -s_coef[s] : s_coef[s];
+                    }
+                }
+                const unsigned vm = __ballot_sync(FULL_MASK, k != sentinel);
+                const int cnt = __popc(vm);  // valid keys are a prefix of the window
+                if (cnt < 32) end = jb + cnt;
+                for (int q = 0; q < cnt; q += 2) {
+                    const bool two = q + 1 < cnt;
+                    const uint32_t k0 = __shfl_sync(FULL_MASK, k, q);
+                    const uint32_t a0 = __shfl_sync(FULL_MASK, wa, q);
+                    const uint32_t b0 = __shfl_sync(FULL_MASK, wb, q);
+                    const float c0 = __shfl_sync(FULL_MASK, cf, q);
+                    const uint32_t k1 = __shfl_sync(FULL_MASK, k, (q + 1) & 31);
+                    const uint32_t a1 = __shfl_sync(FULL_MASK, wa, (q + 1) & 31);
+                    const uint32_t b1 = __shfl_sync(FULL_MASK, wb, (q + 1) & 31);
+                    const float c1 = __shfl_sync(FULL_MASK, cf, (q + 1) & 31);
+                    V xa0[COLS], xb0[COLS], xa1[COLS], xb1[COLS];
 #pragma unroll
-                        for (int t = 0; t < COORD_BLOCK / 32; ++t) {
-                            const int x = cb + t * 32 + int(lane);
-                            if (x < dim) part[size_t(slot) * dim + x] = acc[t];
-                            acc[t] = 0.0f;
+                    for (int t = 0; t < COLS; ++t) {
+                        const int x = cb + t * 32 + int(lane);
+                        vzero(xa0[t]);
+                        vzero(xb0[t]);
+                        vzero(xa1[t]);
+                        vzero(xb1[t]);
+                        if (x < nv) {
+                            xa0[t] = __ldg(vv + size_t(a0) * nv + x);
+                            xb0[t] = __ldg(vv + size_t(b0) * nv + x);
+                            if (two) {
+                                xa1[t] = __ldg(vv + size_t(a1) * nv + x);
+                                xb1[t] = __ldg(vv + size_t(b1) * nv + x);
+                            }
                         }
                     }
-                    ++slot;
-                    if (lane == 0 && cb == 0) part_word[slot] = kq;
-                    prev = kq;
-                }
-                const uint32_t s = eq >> 1;
-                const float coef = (eq & 1u) ? -s_coef[s] : s_coef[s];
-                const float* xa = vocab + size_t(s_wa[s]) * dim;
-                const float* xb = vocab + size_t(s_wb[s]) * dim;
+                    if (k0 != cur) {
+                        flush_run<V>(acc, cur, rs, jb + q, rc, cb, nv, lane, gv, pv);
+                        cur = k0;
+                        rs = jb + q;
+                    }
 #pragma unroll
-                for (int t = 0; t < COORD_BLOCK / 32; ++t) {
-                    const int x = cb + t * 32 + int(lane);
-                    if (x < dim) acc[t] = fmaf(coef, __ldg(xa + x) - __ldg(xb + x), acc[t]);
+                    for (int t = 0; t < COLS; ++t) vfma_diff(acc[t], c0, xa0[t], xb0[t]);
+                    if (two) {
+                        if (k1 != cur) {
+                            flush_run<V>(acc, cur, rs, jb + q + 1, rc, cb, nv, lane, gv, pv);
+                            cur = k1;
+                            rs = jb + q + 1;
+                        }
+#pragma unroll
+                        for (int t = 0; t < COLS; ++t) vfma_diff(acc[t], c1, xa1[t], xb1[t]);
+                    }
                 }
             }
-            if (slot >= run_off[c]) {
-#pragma unroll
-                for (int t = 0; t < COORD_BLOCK / 32; ++t) {
-                    const int x = cb + t * 32 + int(lane);
-                    if (x < dim) part[size_t(slot) * dim + x] = acc[t];
-                }
-            }
+            flush_run<V>(acc, cur, rs, end, rc, cb, nv, lane, gv, pv);
+        }
+        if (lane == 0) {
+            part_word[2 * c] = rc.used_a;
+            part_word[2 * c + 1] = rc.used_b;
+            if (rc.used_b != sentinel) heads[atomicAdd(n_heads, 1u)] = uint32_t(c);
         }
     }
 }
 
-__global__ void k_bwd_finalize(const uint32_t* __restrict__ part_word, const float* __restrict__ part,
-                               const int64_t* __restrict__ n_part_dev, int dim, float* __restrict__ grad) {
-    const int64_t n_part = *n_part_dev;
-    const int64_t warps = int64_t(gridDim.x) * (blockDim.x / 32);
-    const unsigned lane = lane_id();
-    for (int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) / 32; i < n_part; i += warps) {
-        const uint32_t w = part_word[i];
-        if (i > 0 && part_word[i - 1] == w) continue;
-        int64_t end = i + 1;
-        while (end < n_part && part_word[end] == w) ++end;
-        for (int x = lane; x < dim; x += 32) {
-            float s = 0.0f;
-            for (int64_t j = i; j < end; ++j) s += part[size_t(j) * dim + x];
-            grad[size_t(w) * dim + x] += s;
+// Step 4: one CTA per chain head (persistent over the head list).
+template <int VEC>
+__global__ void __launch_bounds__(CHAIN_WARPS * 32) k_bwd_chains(const uint32_t* __restrict__ heads,
+                                                                 const uint32_t* __restrict__ n_heads,
+                                                                 const uint32_t* __restrict__ part_word,
+                                                                 const float* __restrict__ part, int64_t n_chunks,
+                                                                 int dim, float* __restrict__ grad) {
+    using V = typename VecOf<VEC>::T;
+    __shared__ V red[CHAIN_WARPS][32 * COLS];
+    __shared__ int chain_len;
+    const int nv = dim / VEC;
+    const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+    const V* pv = reinterpret_cast<const V*>(part);
+    V* gv = reinterpret_cast<V*>(grad);
+    const uint32_t nh = *n_heads;
+    for (uint32_t h = blockIdx.x; h < nh; h += gridDim.x) {
+        const int64_t c0 = heads[h];
+        const uint32_t w = part_word[2 * c0 + 1];
+        if (warp == 0) {  // chain length: B(c0) plus the A slots of w that follow
+            int64_t m = 1;
+            for (int64_t base = c0 + 1; base < n_chunks; base += 32) {
+                const int64_t cc = base + lane;
+                const bool same = cc < n_chunks && part_word[2 * cc] == w;
+                const unsigned b = __ballot_sync(FULL_MASK, same);
+                const int run = __ffs(~b) - 1;  // leading matches (b == all ones -> -1)
+                m += run < 0 ? 32 : run;
+                if (run >= 0) break;
+            }
+            if (lane == 0) chain_len = int(m);
+        }
+        __syncthreads();
+        const int m = chain_len;
+        for (int cb = 0; cb < nv; cb += 32 * COLS) {
+            V acc[COLS];
+#pragma unroll
+            for (int t = 0; t < COLS; ++t) vzero(acc[t]);
+            for (int i = int(warp); i < m; i += CHAIN_WARPS) {
+                const int64_t slot = i == 0 ? 2 * c0 + 1 : 2 * (c0 + i);
+#pragma unroll
+                for (int t = 0; t < COLS; ++t) {
+                    const int x = cb + t * 32 + int(lane);
+                    if (x < nv) vadd(acc[t], pv[size_t(slot) * nv + x]);
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < COLS; ++t) red[warp][t * 32 + lane] = acc[t];
+            __syncthreads();
+            if (warp == 0) {
+#pragma unroll
+                for (int t = 0; t < COLS; ++t) {
+                    const int x = cb + t * 32 + int(lane);
+                    V s = red[0][t * 32 + lane];
+#pragma unroll
+                    for (int r = 1; r < CHAIN_WARPS; ++r) vadd(s, red[r][t * 32 + lane]);
+                    if (x < nv) {
+                        V g = gv[size_t(w) * nv + x];
+                        vadd(g, s);
+                        gv[size_t(w) * nv + x] = g;
+                    }
+                }
+            }
+            __syncthreads();
         }
     }
 }
@@ -168,11 +328,10 @@ struct BwdLayout {
     uint32_t* s_wa;
     uint32_t* s_wb;
     float* s_coef;
-    int64_t* runs;
-    int64_t* scan_tmp;
     uint32_t* part_word;
     float* part;
-    int64_t max_part;
+    uint32_t* heads;
+    uint32_t* n_heads;
 };
 
 size_t bwd_layout(const ft_tree* t, const ft_flows* f, void* base, BwdLayout* out) {
@@ -186,11 +345,10 @@ size_t bwd_layout(const ft_tree* t, const ft_flows* f, void* base, BwdLayout* ou
     l.s_wa = w.take<uint32_t>(size_t(f->capacity));
     l.s_wb = w.take<uint32_t>(size_t(f->capacity));
     l.s_coef = w.take<float>(size_t(f->capacity));
-    l.runs = w.take<int64_t>(size_t(n_chunks) + 1);
-    l.scan_tmp = w.take<int64_t>(ft_scan_tmp_elems(n_chunks + 1));
-    l.max_part = std::min<int64_t>(ne, n_chunks + t->n + 1);
-    l.part_word = w.take<uint32_t>(size_t(l.max_part));
-    l.part = w.take<float>(size_t(l.max_part) * t->dim);
+    l.part_word = w.take<uint32_t>(size_t(2 * n_chunks));
+    l.part = w.take<float>(size_t(2 * n_chunks) * t->dim);
+    l.heads = w.take<uint32_t>(size_t(n_chunks));
+    l.n_heads = w.take<uint32_t>(1);
     if (out) *out = l;
     return w.off + 256;
 }
@@ -226,14 +384,23 @@ extern "C" ft_status ft_flowtree_backward(const ft_tree* t, const ft_docs* a, co
         grad_cost_dev, t->levels, sentinel, l.key, l.s_wa, l.s_wb, l.s_coef);
     FT_TRY(ft_iota_u32(l.perm, ne, s));
     FT_TRY(ft_sort_perm_by_u32(l.key, l.perm, ne, key_bits, l.sort_tmp, s));
-    k_bwd_chunk_runs<<<grid_for(n_chunks, 256), 256, 0, s>>>(l.key, l.perm, ne, sentinel, n_chunks, l.runs);
-    FT_CUDA(cudaMemsetAsync(l.runs + n_chunks, 0, 8, s));
-    FT_TRY(ft_exclusive_scan_i64(l.runs, l.runs, n_chunks + 1, l.scan_tmp, s));
-    k_bwd_partials<<<grid_for(n_chunks * 32, 256), 256, 0, s>>>(l.key, l.perm, ne, sentinel, n_chunks, l.runs,
-                                                                l.s_wa, l.s_wb, l.s_coef, vocab_dev, t->dim,
-                                                                l.part_word, l.part);
-    k_bwd_finalize<<<grid_for(l.max_part * 32, 256), 256, 0, s>>>(l.part_word, l.part, l.runs + n_chunks, t->dim,
-                                                                  grad_vocab_dev);
+    FT_CUDA(cudaMemsetAsync(l.n_heads, 0, sizeof(uint32_t), s));
+    const int dim = t->dim;
+    const bool vec4 = dim % 4 == 0 && (reinterpret_cast<uintptr_t>(vocab_dev) & 15u) == 0 &&
+                      (reinterpret_cast<uintptr_t>(grad_vocab_dev) & 15u) == 0;
+    const int grid_runs = grid_for(n_chunks * 32, 256);
+    const int grid_chains = int(std::max<int64_t>(1, std::min<int64_t>(n_chunks, int64_t(t->num_sms) * 8)));
+    if (vec4) {
+        k_bwd_runs<4><<<grid_runs, 256, 0, s>>>(l.key, l.perm, ne, sentinel, l.s_wa, l.s_wb, l.s_coef, vocab_dev, dim,
+                                                grad_vocab_dev, l.part_word, l.part, l.heads, l.n_heads);
+        k_bwd_chains<4><<<grid_chains, CHAIN_WARPS * 32, 0, s>>>(l.heads, l.n_heads, l.part_word, l.part, n_chunks,
+                                                                 dim, grad_vocab_dev);
+    } else {
+        k_bwd_runs<1><<<grid_runs, 256, 0, s>>>(l.key, l.perm, ne, sentinel, l.s_wa, l.s_wb, l.s_coef, vocab_dev, dim,
+                                                grad_vocab_dev, l.part_word, l.part, l.heads, l.n_heads);
+        k_bwd_chains<1><<<grid_chains, CHAIN_WARPS * 32, 0, s>>>(l.heads, l.n_heads, l.part_word, l.part, n_chunks,
+                                                                 dim, grad_vocab_dev);
+    }
     FT_CUDA(cudaGetLastError());
     return FT_OK;
 }

@@ -129,3 +129,60 @@ def test_finite_differences_with_rebuilt_tree_away_from_cell_edges():
         if checked >= 12:
             break
     assert checked >= 4
+
+
+@pytest.mark.parametrize("dim,n_words,n_pairs", [(2, 400, 160), (7, 500, 120), (300, 800, 96), (520, 600, 48)])
+def test_backward_any_dimension_and_long_runs(dim, n_words, n_pairs):
+    # Dimensions that are not a multiple of 4 (scalar row loads), above one
+    # column block (520 > 384), and small vocabularies, so that the frequent
+    # words' contributions span many chunks of the sorted list.
+    V = synth.mixture_vocab(n_words, dim, 12, 0.3, 610 + dim)
+    shift = synth.random_shift(dim, 611 + dim)
+    rng = np.random.default_rng(612 + dim)
+    A = synth.zipf_docs(n_words, n_pairs, 613 + dim, lengths=rng.integers(20, 301, n_pairs))
+    B = synth.zipf_docs(n_words, n_pairs, 614 + dim, lengths=rng.integers(20, 301, n_pairs))
+    tree = api.Tree(torch.as_tensor(V, device="cuda"), 12, shift)
+    ot = O.OracleTree(V, 12, shift)
+    DA, DB = api.Docs.from_csr(tree, A), api.Docs.from_csr(tree, B)
+    pa = np.arange(n_pairs)
+    g = np.random.default_rng(615).standard_normal(n_pairs).astype(np.float32)
+    flows = api.Flows(tree, DA, DB, pa, pa)
+    api.flowtree_batch(tree, tree.points, DA, DB, flows.pair_a, flows.pair_b, flows=flows)
+    gc = torch.as_tensor(g, device="cuda")
+    grad = api.flowtree_backward(tree, DA, DB, flows, tree.points, gc)
+    got = grad.cpu().numpy().astype(np.float64)
+    SA = ot.embed_docs(A.row_ptr, A.word, A.weight)
+    SB = ot.embed_docs(B.row_ptr, B.word, B.weight)
+    ref = ot.grad_batch(V, SA, SB, pa, pa, g.astype(np.float64))
+    scale = max(1.0, float(np.abs(ref).max()))
+    assert np.abs(got - ref).max() <= 1e-4 * scale
+    assert torch.equal(grad, api.flowtree_backward(tree, DA, DB, flows, tree.points, gc))
+    touched = np.zeros(n_words, bool)
+    touched[A.word] = True
+    touched[B.word] = True
+    assert np.all(got[~touched] == 0.0)
+
+
+def test_backward_single_point_runs_over_many_chunks():
+    # Every pair moves all of its mass from point 0 to point 1: the sorted
+    # contributions are n_pairs entries of point 0 then n_pairs of point 1,
+    # each run crossing many chunk boundaries.  Closed form:
+    #   grad[0] = sum_i g_i (x0 - x1)/||x0 - x1||,  grad[1] = -grad[0].
+    n_pairs = 5000
+    V = np.array([[0.1, 0.2, 0.3, 0.4], [0.9, -0.5, 0.25, 0.0], [0.5, 0.5, 0.5, 0.5]], np.float32)
+    tree = api.Tree(torch.as_tensor(V, device="cuda"), 12, synth.random_shift(4, 620))
+    DA = api.Docs.from_csr(tree, synth.csr_from_lists([[0]] * n_pairs))
+    DB = api.Docs.from_csr(tree, synth.csr_from_lists([[1]] * n_pairs))
+    g = np.random.default_rng(621).standard_normal(n_pairs)
+    pa = np.arange(n_pairs)
+    flows = api.Flows(tree, DA, DB, pa, pa)
+    api.flowtree_batch(tree, tree.points, DA, DB, flows.pair_a, flows.pair_b, flows=flows)
+    grad = api.flowtree_backward(tree, DA, DB, flows, tree.points, torch.as_tensor(g, dtype=torch.float32,
+                                                                                    device="cuda"))
+    got = grad.cpu().numpy().astype(np.float64)
+    d = V[0].astype(np.float64) - V[1].astype(np.float64)
+    u = d / np.linalg.norm(d)
+    gs = float(g.astype(np.float32).astype(np.float64).sum())
+    assert np.allclose(got[0], gs * u, rtol=1e-5, atol=1e-4)
+    assert np.allclose(got[1], -gs * u, rtol=1e-5, atol=1e-4)
+    assert np.all(got[2] == 0.0)
