@@ -15,10 +15,10 @@
 //      cut by a chunk boundary goes to one of the chunk's two partial slots
 //      (A: the run that continues from the previous chunk, B: the run that
 //      starts in this chunk and continues into the next);
-//   4. every B slot starts a chain B(c), A(c+1), A(c+2), ... of one point;
-//      a CTA per chain sums it in a fixed order (warp r takes elements r,
-//      r + 8, ...; the eight warp sums are then added in warp order) and adds
-//      the total to grad.
+//   4. every B slot starts a chain B(c), A(c+1), A(c+2), ... of one point.
+//      A warp sums a chain of at most 16 elements in order; a longer chain
+//      gets a CTA, whose warp r sums elements r, r + 8, ... and whose eight
+//      warp sums are then added in warp order.  The total goes to grad.
 // Rows are read as float4 when the dimension and the pointers allow it.
 #include <algorithm>
 #include <cstdint>
@@ -29,7 +29,9 @@ namespace {
 
 constexpr int CHUNK = 64;       // sorted contributions per warp
 constexpr int COLS = 3;         // row vectors per lane in one column block (block = 96 vectors)
-constexpr int CHAIN_WARPS = 8;  // warps per chain CTA
+constexpr int CHAIN_WARPS = 8;  // warps per CTA of a long chain
+constexpr int SHORT_CHAIN = 16; // longest chain one warp sums alone
+constexpr int BATCH = 4;        // contributions whose rows are loaded together
 
 __device__ __forceinline__ void vzero(float& a) { a = 0.0f; }
 __device__ __forceinline__ void vzero(float4& a) { a = make_float4(0.0f, 0.0f, 0.0f, 0.0f); }
@@ -145,10 +147,14 @@ __device__ __forceinline__ void flush_run(V (&acc)[COLS], uint32_t cur, int64_t 
     for (int t = 0; t < COLS; ++t) vzero(acc[t]);
 }
 
-// Step 3: one warp per chunk of CHUNK sorted contributions.  Lane q of a
-// 32-entry window holds contribution q (its point, both rows and the signed
-// coefficient); the warp walks the window in order, two contributions at a
-// time so that four row loads per column are in flight.
+// Step 3: one warp per chunk of CHUNK sorted contributions.  Every
+// contribution of a run updates the run's own point w, and for both
+// endpoints it is coef * (x_w - x_other) (for the nu endpoint,
+// -coef (x_a - x_b) = coef (x_b - x_a), the same floating-point value), so
+// each contribution gathers only the other endpoint's row; x_w is loaded once
+// per run.  Lane q of a 32-entry window holds contribution q (point, other
+// point, coefficient); the warp walks the window in order, BATCH
+// contributions at a time with their row loads in flight together.
 template <int VEC>
 __global__ void __launch_bounds__(256) k_bwd_runs(const uint32_t* __restrict__ key, const uint32_t* __restrict__ perm,
                                                   int64_t n, uint32_t sentinel, const uint32_t* __restrict__ s_wa,
@@ -170,71 +176,62 @@ __global__ void __launch_bounds__(256) k_bwd_runs(const uint32_t* __restrict__ k
         const uint32_t k_after = j1 < n ? key[perm[j1]] : sentinel;
         RunChunk rc{c, j0, j1, k_before, k_after, sentinel, sentinel, sentinel};
         for (int cb = 0; cb < nv; cb += 32 * COLS) {
-            V acc[COLS];
+            V acc[COLS], xw[COLS];
 #pragma unroll
-            for (int t = 0; t < COLS; ++t) vzero(acc[t]);
+            for (int t = 0; t < COLS; ++t) {
+                vzero(acc[t]);
+                vzero(xw[t]);
+            }
             uint32_t cur = sentinel;  // point of the open run
             int64_t rs = j0;          // where it started
-            int64_t end = j1;  // first sentinel (sentinels sort last)
+            int64_t end = j1;         // first sentinel (sentinels sort last)
             for (int64_t jb = j0; jb < end; jb += 32) {
                 const int64_t j = jb + lane;
-                uint32_t k = sentinel, wa = 0, wb = 0;
+                uint32_t k = sentinel, o = 0;
                 float cf = 0.0f;
                 if (j < end) {
                     const uint32_t e = perm[j];
                     k = key[e];
                     if (k != sentinel) {
                         const uint32_t s = e >> 1;
-                        wa = s_wa[s];
-                        wb = s_wb[s];
-                        cf = (e & 1u) ? -s_coef[s] : s_coef[s];
+                        o = (e & 1u) ? s_wa[s] : s_wb[s];
+                        cf = s_coef[s];
                     }
                 }
                 const unsigned vm = __ballot_sync(FULL_MASK, k != sentinel);
                 const int cnt = __popc(vm);  // valid keys are a prefix of the window
                 if (cnt < 32) end = jb + cnt;
-                for (int q = 0; q < cnt; q += 2) {
-                    const bool two = q + 1 < cnt;
-                    const uint32_t k0 = __shfl_sync(FULL_MASK, k, q);
-                    const uint32_t a0 = __shfl_sync(FULL_MASK, wa, q);
-                    const uint32_t b0 = __shfl_sync(FULL_MASK, wb, q);
-                    const float c0 = __shfl_sync(FULL_MASK, cf, q);
-                    const uint32_t k1 = __shfl_sync(FULL_MASK, k, (q + 1) & 31);
-                    const uint32_t a1 = __shfl_sync(FULL_MASK, wa, (q + 1) & 31);
-                    const uint32_t b1 = __shfl_sync(FULL_MASK, wb, (q + 1) & 31);
-                    const float c1 = __shfl_sync(FULL_MASK, cf, (q + 1) & 31);
-                    V xa0[COLS], xb0[COLS], xa1[COLS], xb1[COLS];
+                for (int q = 0; q < cnt; q += BATCH) {
+                    // the other endpoints' rows of BATCH contributions in flight
+                    V xo[BATCH][COLS];
 #pragma unroll
-                    for (int t = 0; t < COLS; ++t) {
-                        const int x = cb + t * 32 + int(lane);
-                        vzero(xa0[t]);
-                        vzero(xb0[t]);
-                        vzero(xa1[t]);
-                        vzero(xb1[t]);
-                        if (x < nv) {
-                            xa0[t] = __ldg(vv + size_t(a0) * nv + x);
-                            xb0[t] = __ldg(vv + size_t(b0) * nv + x);
-                            if (two) {
-                                xa1[t] = __ldg(vv + size_t(a1) * nv + x);
-                                xb1[t] = __ldg(vv + size_t(b1) * nv + x);
+                    for (int u = 0; u < BATCH; ++u) {
+                        const uint32_t ou = __shfl_sync(FULL_MASK, o, (q + u) & 31);
+#pragma unroll
+                        for (int t = 0; t < COLS; ++t) {
+                            const int x = cb + t * 32 + int(lane);
+                            vzero(xo[u][t]);
+                            if (x < nv && q + u < cnt) xo[u][t] = __ldg(vv + size_t(ou) * nv + x);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < BATCH; ++u) {
+                        const uint32_t ku = __shfl_sync(FULL_MASK, k, (q + u) & 31);
+                        const float cu = __shfl_sync(FULL_MASK, cf, (q + u) & 31);
+                        if (q + u < cnt) {
+                            if (ku != cur) {  // a run starts: load its own row
+                                flush_run<V>(acc, cur, rs, jb + q + u, rc, cb, nv, lane, gv, pv);
+                                cur = ku;
+                                rs = jb + q + u;
+#pragma unroll
+                                for (int t = 0; t < COLS; ++t) {
+                                    const int x = cb + t * 32 + int(lane);
+                                    if (x < nv) xw[t] = __ldg(vv + size_t(ku) * nv + x);
+                                }
                             }
-                        }
-                    }
-                    if (k0 != cur) {
-                        flush_run<V>(acc, cur, rs, jb + q, rc, cb, nv, lane, gv, pv);
-                        cur = k0;
-                        rs = jb + q;
-                    }
 #pragma unroll
-                    for (int t = 0; t < COLS; ++t) vfma_diff(acc[t], c0, xa0[t], xb0[t]);
-                    if (two) {
-                        if (k1 != cur) {
-                            flush_run<V>(acc, cur, rs, jb + q + 1, rc, cb, nv, lane, gv, pv);
-                            cur = k1;
-                            rs = jb + q + 1;
+                            for (int t = 0; t < COLS; ++t) vfma_diff(acc[t], cu, xw[t], xo[u][t]);
                         }
-#pragma unroll
-                        for (int t = 0; t < COLS; ++t) vfma_diff(acc[t], c1, xa1[t], xb1[t]);
                     }
                 }
             }
@@ -248,44 +245,102 @@ __global__ void __launch_bounds__(256) k_bwd_runs(const uint32_t* __restrict__ k
     }
 }
 
-// Step 4: one CTA per chain head (persistent over the head list).
+// Length of the chain that starts at B(c0) of point w: B(c0) plus the A
+// slots of w that follow (whole warp; the result is on every lane).
+__device__ __forceinline__ int chain_length(const uint32_t* __restrict__ part_word, int64_t n_chunks, int64_t c0,
+                                            uint32_t w) {
+    const unsigned lane = lane_id();
+    int m = 1;
+    for (int64_t base = c0 + 1; base < n_chunks; base += 32) {
+        const int64_t cc = base + lane;
+        const bool same = cc < n_chunks && part_word[2 * cc] == w;
+        const unsigned b = __ballot_sync(FULL_MASK, same);
+        const int run = __ffs(~b) - 1;  // leading matches (b == all ones -> -1)
+        m += run < 0 ? 32 : run;
+        if (run >= 0) break;
+    }
+    return m;
+}
+
+__device__ __forceinline__ int64_t chain_slot(int64_t c0, int i) { return i == 0 ? 2 * c0 + 1 : 2 * (c0 + i); }
+
+// Step 4a: a warp per chain head.  A chain of at most SHORT_CHAIN elements is
+// summed by the warp in order and added to grad; a longer one goes to the
+// list of long chains.
 template <int VEC>
-__global__ void __launch_bounds__(CHAIN_WARPS * 32) k_bwd_chains(const uint32_t* __restrict__ heads,
-                                                                 const uint32_t* __restrict__ n_heads,
-                                                                 const uint32_t* __restrict__ part_word,
-                                                                 const float* __restrict__ part, int64_t n_chunks,
-                                                                 int dim, float* __restrict__ grad) {
+__global__ void __launch_bounds__(256) k_bwd_chains(const uint32_t* __restrict__ heads,
+                                                    const uint32_t* __restrict__ counters,
+                                                    const uint32_t* __restrict__ part_word,
+                                                    const float* __restrict__ part, int64_t n_chunks, int dim,
+                                                    float* __restrict__ grad, uint32_t* __restrict__ long_heads,
+                                                    uint32_t* __restrict__ n_long) {
+    using V = typename VecOf<VEC>::T;
+    const int nv = dim / VEC;
+    const unsigned lane = lane_id();
+    const V* pv = reinterpret_cast<const V*>(part);
+    V* gv = reinterpret_cast<V*>(grad);
+    const uint32_t nh = counters[0];
+    const uint32_t warps = gridDim.x * (blockDim.x >> 5);
+    for (uint32_t h = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; h < nh; h += warps) {
+        const int64_t c0 = heads[h];
+        const uint32_t w = part_word[2 * c0 + 1];
+        const int m = chain_length(part_word, n_chunks, c0, w);
+        if (m > SHORT_CHAIN) {
+            if (lane == 0) long_heads[atomicAdd(n_long, 1u)] = uint32_t(c0);
+            continue;
+        }
+        for (int cb = 0; cb < nv; cb += 32 * COLS) {
+            V acc[COLS];
+#pragma unroll
+            for (int t = 0; t < COLS; ++t) vzero(acc[t]);
+            for (int i = 0; i < m; ++i) {
+                const int64_t slot = chain_slot(c0, i);
+#pragma unroll
+                for (int t = 0; t < COLS; ++t) {
+                    const int x = cb + t * 32 + int(lane);
+                    if (x < nv) vadd(acc[t], pv[size_t(slot) * nv + x]);
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < COLS; ++t) {
+                const int x = cb + t * 32 + int(lane);
+                if (x < nv) {
+                    V g = gv[size_t(w) * nv + x];
+                    vadd(g, acc[t]);
+                    gv[size_t(w) * nv + x] = g;
+                }
+            }
+        }
+    }
+}
+
+// Step 4b: a CTA per long chain (persistent over the list): warp r sums
+// elements r, r + CHAIN_WARPS, ... in order, then the warp sums are added in
+// warp order.
+template <int VEC>
+__global__ void __launch_bounds__(CHAIN_WARPS * 32) k_bwd_long_chains(const uint32_t* __restrict__ long_heads,
+                                                                      const uint32_t* __restrict__ n_long,
+                                                                      const uint32_t* __restrict__ part_word,
+                                                                      const float* __restrict__ part,
+                                                                      int64_t n_chunks, int dim,
+                                                                      float* __restrict__ grad) {
     using V = typename VecOf<VEC>::T;
     __shared__ V red[CHAIN_WARPS][32 * COLS];
-    __shared__ int chain_len;
     const int nv = dim / VEC;
     const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
     const V* pv = reinterpret_cast<const V*>(part);
     V* gv = reinterpret_cast<V*>(grad);
-    const uint32_t nh = *n_heads;
-    for (uint32_t h = blockIdx.x; h < nh; h += gridDim.x) {
-        const int64_t c0 = heads[h];
+    const uint32_t nl = *n_long;
+    for (uint32_t h = blockIdx.x; h < nl; h += gridDim.x) {
+        const int64_t c0 = long_heads[h];
         const uint32_t w = part_word[2 * c0 + 1];
-        if (warp == 0) {  // chain length: B(c0) plus the A slots of w that follow
-            int64_t m = 1;
-            for (int64_t base = c0 + 1; base < n_chunks; base += 32) {
-                const int64_t cc = base + lane;
-                const bool same = cc < n_chunks && part_word[2 * cc] == w;
-                const unsigned b = __ballot_sync(FULL_MASK, same);
-                const int run = __ffs(~b) - 1;  // leading matches (b == all ones -> -1)
-                m += run < 0 ? 32 : run;
-                if (run >= 0) break;
-            }
-            if (lane == 0) chain_len = int(m);
-        }
-        __syncthreads();
-        const int m = chain_len;
+        const int m = chain_length(part_word, n_chunks, c0, w);  // every warp, same value
         for (int cb = 0; cb < nv; cb += 32 * COLS) {
             V acc[COLS];
 #pragma unroll
             for (int t = 0; t < COLS; ++t) vzero(acc[t]);
             for (int i = int(warp); i < m; i += CHAIN_WARPS) {
-                const int64_t slot = i == 0 ? 2 * c0 + 1 : 2 * (c0 + i);
+                const int64_t slot = chain_slot(c0, i);
 #pragma unroll
                 for (int t = 0; t < COLS; ++t) {
                     const int x = cb + t * 32 + int(lane);
@@ -331,7 +386,8 @@ struct BwdLayout {
     uint32_t* part_word;
     float* part;
     uint32_t* heads;
-    uint32_t* n_heads;
+    uint32_t* long_heads;
+    uint32_t* counters;  // [0] chain heads, [1] long chains
 };
 
 size_t bwd_layout(const ft_tree* t, const ft_flows* f, void* base, BwdLayout* out) {
@@ -348,7 +404,8 @@ size_t bwd_layout(const ft_tree* t, const ft_flows* f, void* base, BwdLayout* ou
     l.part_word = w.take<uint32_t>(size_t(2 * n_chunks));
     l.part = w.take<float>(size_t(2 * n_chunks) * t->dim);
     l.heads = w.take<uint32_t>(size_t(n_chunks));
-    l.n_heads = w.take<uint32_t>(1);
+    l.long_heads = w.take<uint32_t>(size_t(n_chunks));
+    l.counters = w.take<uint32_t>(2);
     if (out) *out = l;
     return w.off + 256;
 }
@@ -384,22 +441,27 @@ extern "C" ft_status ft_flowtree_backward(const ft_tree* t, const ft_docs* a, co
         grad_cost_dev, t->levels, sentinel, l.key, l.s_wa, l.s_wb, l.s_coef);
     FT_TRY(ft_iota_u32(l.perm, ne, s));
     FT_TRY(ft_sort_perm_by_u32(l.key, l.perm, ne, key_bits, l.sort_tmp, s));
-    FT_CUDA(cudaMemsetAsync(l.n_heads, 0, sizeof(uint32_t), s));
+    FT_CUDA(cudaMemsetAsync(l.counters, 0, 2 * sizeof(uint32_t), s));
     const int dim = t->dim;
     const bool vec4 = dim % 4 == 0 && (reinterpret_cast<uintptr_t>(vocab_dev) & 15u) == 0 &&
                       (reinterpret_cast<uintptr_t>(grad_vocab_dev) & 15u) == 0;
     const int grid_runs = grid_for(n_chunks * 32, 256);
-    const int grid_chains = int(std::max<int64_t>(1, std::min<int64_t>(n_chunks, int64_t(t->num_sms) * 8)));
+    const int grid_chains = int(std::max<int64_t>(1, std::min<int64_t>((n_chunks + 7) / 8, int64_t(t->num_sms) * 8)));
+    const int grid_long = std::max(1, t->num_sms * 2);
     if (vec4) {
         k_bwd_runs<4><<<grid_runs, 256, 0, s>>>(l.key, l.perm, ne, sentinel, l.s_wa, l.s_wb, l.s_coef, vocab_dev, dim,
-                                                grad_vocab_dev, l.part_word, l.part, l.heads, l.n_heads);
-        k_bwd_chains<4><<<grid_chains, CHAIN_WARPS * 32, 0, s>>>(l.heads, l.n_heads, l.part_word, l.part, n_chunks,
-                                                                 dim, grad_vocab_dev);
+                                                grad_vocab_dev, l.part_word, l.part, l.heads, l.counters);
+        k_bwd_chains<4><<<grid_chains, 256, 0, s>>>(l.heads, l.counters, l.part_word, l.part, n_chunks, dim,
+                                                    grad_vocab_dev, l.long_heads, l.counters + 1);
+        k_bwd_long_chains<4><<<grid_long, CHAIN_WARPS * 32, 0, s>>>(l.long_heads, l.counters + 1, l.part_word, l.part,
+                                                                    n_chunks, dim, grad_vocab_dev);
     } else {
         k_bwd_runs<1><<<grid_runs, 256, 0, s>>>(l.key, l.perm, ne, sentinel, l.s_wa, l.s_wb, l.s_coef, vocab_dev, dim,
-                                                grad_vocab_dev, l.part_word, l.part, l.heads, l.n_heads);
-        k_bwd_chains<1><<<grid_chains, CHAIN_WARPS * 32, 0, s>>>(l.heads, l.n_heads, l.part_word, l.part, n_chunks,
-                                                                 dim, grad_vocab_dev);
+                                                grad_vocab_dev, l.part_word, l.part, l.heads, l.counters);
+        k_bwd_chains<1><<<grid_chains, 256, 0, s>>>(l.heads, l.counters, l.part_word, l.part, n_chunks, dim,
+                                                    grad_vocab_dev, l.long_heads, l.counters + 1);
+        k_bwd_long_chains<1><<<grid_long, CHAIN_WARPS * 32, 0, s>>>(l.long_heads, l.counters + 1, l.part_word, l.part,
+                                                                    n_chunks, dim, grad_vocab_dev);
     }
     FT_CUDA(cudaGetLastError());
     return FT_OK;
