@@ -73,6 +73,9 @@ def parse():
     ap.add_argument("--profile-exact", nargs=2, type=int, metavar=("N_Q", "PER_Q"),
                     help="only run exact W1 on N_Q text-shaped queries x PER_Q random documents of 20,000 "
                          "(vocabulary 100,000 x 300) three times (a case for ncu); no timing")
+    ap.add_argument("--profile-backward", type=int, metavar="N_PAIRS",
+                    help="only run forward (flows saved) + backward on N_PAIRS pairs of the differentiation workload "
+                         "(vocabulary 30,000 x 300) three times (a case for ncu); no timing")
     return ap.parse_args()
 
 
@@ -127,6 +130,24 @@ def profile_exact(args):
         api.exact_w1(tree, tree.points, Q, D, pa, pb, workspace=ws)
     torch.cuda.synchronize()
     print("profile exact done: %d pairs, status %d" % (n_q * per_q, tree.status()))
+
+
+def profile_backward(args):
+    import torch
+    from paper_1910_04126_gb300 import api, synth
+    n = args.profile_backward
+    wl = synth.diff_pairs(n_words=30000, n_pairs=n)
+    tree = api.Tree(torch.as_tensor(wl.points, device="cuda"), wl.levels, wl.shift)
+    A, B = api.Docs.from_csr(tree, wl.db), api.Docs.from_csr(tree, wl.queries)
+    idx = torch.arange(n, dtype=torch.int32, device="cuda")
+    flows = api.Flows(tree, A, B, idx, idx)
+    gcost = torch.ones(n, device="cuda")
+    gv = torch.zeros_like(tree.points)
+    for _ in range(3):
+        api.flowtree_batch(tree, tree.points, A, B, flows.pair_a, flows.pair_b, flows=flows)
+        api.flowtree_backward(tree, A, B, flows, tree.points, gcost, grad_vocab=gv)
+    torch.cuda.synchronize()
+    print("profile backward done: %d pairs, status %d" % (n, tree.status()))
 
 
 # ---------------------------------------------------------------------------
@@ -285,6 +306,9 @@ def main():
         return
     if args.profile_exact:
         profile_exact(args)
+        return
+    if args.profile_backward:
+        profile_backward(args)
         return
 
     import torch
