@@ -239,10 +239,22 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const uint32_t* __res
     cnt[threadIdx.x] = 0;
     __syncthreads();
     const int64_t tile0 = int64_t(blockIdx.x) * RS_TILE;
+    // all of the tile's loads first (the digit is a gather through perm)
+    uint32_t ev[RS_ITEMS], dv[RS_ITEMS];
 #pragma unroll
     for (int r = 0; r < RS_ITEMS; ++r) {
-        int64_t i = tile0 + int64_t(r) * RS_THREADS + threadIdx.x;
-        if (i < n) atomicAdd(&cnt[digit(perm[i])], 1u);
+        const int64_t i = tile0 + int64_t(r) * RS_THREADS + threadIdx.x;
+        ev[r] = i < n ? perm[i] : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; ++r) {
+        const int64_t i = tile0 + int64_t(r) * RS_THREADS + threadIdx.x;
+        dv[r] = i < n ? digit(ev[r]) : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; ++r) {
+        const int64_t i = tile0 + int64_t(r) * RS_THREADS + threadIdx.x;
+        if (i < n) atomicAdd(&cnt[dv[r]], 1u);
     }
     __syncthreads();
     hist[int64_t(threadIdx.x) * nblocks + blockIdx.x] = cnt[threadIdx.x];
@@ -254,15 +266,31 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const uint32_t* __
                                                               const int64_t* __restrict__ offsets, int nblocks,
                                                               DigitFn digit) {
     __shared__ uint32_t base[256];
+    __shared__ int64_t boff[256];  // this tile's first output position per digit
     __shared__ uint32_t wcnt[RS_THREADS / 32][256];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t tile0 = int64_t(blockIdx.x) * RS_TILE;
     base[tid] = 0;
+    boff[tid] = offsets[int64_t(tid) * nblocks + blockIdx.x];
+    // all of the tile's loads first (the digit is a gather through perm); the
+    // ranking rounds below then work from registers and shared memory
+    uint32_t ev[RS_ITEMS], dv[RS_ITEMS];
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; ++r) {
+        const int64_t i = tile0 + int64_t(r) * RS_THREADS + tid;
+        ev[r] = i < n ? perm_in[i] : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; ++r) {
+        const int64_t i = tile0 + int64_t(r) * RS_THREADS + tid;
+        dv[r] = i < n ? digit(ev[r]) : 0xFFFFFFFFu;
+    }
+#pragma unroll
     for (int r = 0; r < RS_ITEMS; ++r) {
         const int64_t i = tile0 + int64_t(r) * RS_THREADS + tid;
         const bool valid = i < n;
-        const uint32_t e = valid ? perm_in[i] : 0u;
-        const uint32_t d = valid ? digit(e) : 0xFFFFFFFFu;
+        const uint32_t e = ev[r];
+        const uint32_t d = dv[r];
         for (int j = tid; j < (RS_THREADS / 32) * 256; j += RS_THREADS) (&wcnt[0][0])[j] = 0;
         __syncthreads();
         const unsigned peers = __match_any_sync(FULL_MASK, d);
@@ -283,7 +311,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const uint32_t* __
         __syncthreads();
         if (valid) {
             uint32_t local = wcnt[warp][d] + uint32_t(rank_in_warp);
-            perm_out[offsets[int64_t(d) * nblocks + blockIdx.x] + local] = e;
+            perm_out[boff[d] + local] = e;
         }
         __syncthreads();
     }
