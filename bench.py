@@ -508,7 +508,14 @@ def extras(args, tree, D, Q, q_h, db_h, pts, shift, batched_value, dev, pk, pk_k
     e1.record()
     e1.synchronize()
     f_ms = e0.elapsed_time(e1) / reps
+    e0.record()
+    for _ in range(reps):
+        api.flowtree_backward(t2, A, B, flows, t2.points, gcost, grad_vocab=gv, workspace=bws)
+    e1.record()
+    e1.synchronize()
+    b_ms = e0.elapsed_time(e1) / reps
     out["fwd_bwd"] = {"value": npairs / (fb_ms * 1e-3), "unit": UNIT, "forward_only": npairs / (f_ms * 1e-3),
+                      "ms_per_step": fb_ms, "backward_ms": b_ms,
                       "workload": "vocab %d x 300 (1,000-cluster mixture), %d doc pairs, lengths 20-300" % (nw, npairs)}
 
     # text-shaped kNN pipeline
