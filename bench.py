@@ -553,6 +553,7 @@ def extras(args, tree, D, Q, q_h, db_h, pts, shift, batched_value, dev, pk, pk_k
         "scan_pairs_per_s": nqt * ndb / (ms3 * 1e-3), "batch_ms_median": ms3, "graph": True,
         "launch_config": list(tuned3),
         "scan_roofline": scan_roofline(t3, Q3, D3, pk, pk_kind),
+        "flowtree_roofline": text_flowtree_roofline(t3, Q3, D3, tq, tdb, k1, dev, pk, pk_kind),
         "workload": "vocab %d x 300, %d docs (log-normal lengths, Zipf(1.1) words), %d queries, top-%d -> top-%d"
                     % (nwt, ndb, nqt, k1, TOPK)}
 
@@ -727,6 +728,75 @@ def depth_histogram(tree, Q, D, pa, pb):
     return {"sample_pairs": int(len(pa)), "pairs_per_depth": (cnt / cnt.sum()).round(4).tolist(),
             "mass_per_depth": (mass / mass.sum()).round(4).tolist(),
             "matched_pairs_per_pair": float(cnt.sum()) / len(pa)}
+
+
+def read_peak_gbs(dev, nbytes: int, passes: int) -> float:
+    """Read bandwidth of ft_read_probe over an nbytes buffer (median of 5 timed calls after a warm pass)."""
+    import torch
+    from paper_1910_04126_gb300 import api
+    buf = torch.ones(nbytes // 4, dtype=torch.int32, device=dev)
+    sink = torch.zeros(1, dtype=torch.int32, device=dev)
+    api.read_probe(buf, 1, sink)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ts = []
+    for _ in range(5):
+        e0.record()
+        api.read_probe(buf, passes, sink)
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    del buf
+    return nbytes * passes / (statistics.median(ts) * 1e-3) / 1e9
+
+
+def text_flowtree_roofline(tree, Q, D, q_h, db_h, k1, dev, pk, pk_kind):
+    """L2 and HBM roofline of the Flowtree launch of the text pipeline (the same k1 candidates per query,
+    timed alone).  Algorithmic bytes per pair: two 4d-byte rows per priced (distinct-point) matched pair
+    + 8 B per support item + 4 B out, all through L2 (the query's rows are shared by its k1 candidates);
+    the HBM view counts the candidate side once: its rows, supports and the output.  The L2 peak is
+    ft_read_probe over buffers that fit in L2 (the best of 16, 32 and 64 MiB); the priced pairs per pair
+    come from the saved flows of the first 20 queries' candidates."""
+    import torch
+    from paper_1910_04126_gb300 import api
+    nq = Q.n_docs
+    cand = api.quadtree_scan(tree, Q, D, k1).reshape(-1)
+    pa = torch.arange(nq, dtype=torch.int32, device=dev).repeat_interleave(k1)
+    n = int(pa.numel())
+    out = torch.empty(n, dtype=torch.float32, device=dev)
+    ws = torch.empty(api.flowtree_workspace_size(tree, Q, D, n), dtype=torch.uint8, device=dev)
+    api.flowtree_batch(tree, tree.points, Q, D, pa, cand, out=out, workspace=ws)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ts = []
+    for _ in range(5):
+        e0.record()
+        api.flowtree_batch(tree, tree.points, Q, D, pa, cand, out=out, workspace=ws)
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = statistics.median(ts)
+    del ws, out
+    ns = min(nq, 20) * k1
+    flows = api.Flows(tree, Q, D, pa[:ns], cand[:ns])
+    api.flowtree_batch(tree, tree.points, Q, D, flows.pair_a, flows.pair_b, flows=flows)
+    dep = np.concatenate([x[3] for x in flows.export()]).astype(np.int64)
+    priced = float((dep <= LEVELS).sum()) / ns
+    pa_h, pb_h = pa.cpu().numpy(), cand.cpu().numpy()
+    s_q = float(q_h.lengths()[pa_h].mean())
+    s_d = float(db_h.lengths()[pb_h].mean())
+    row = 4.0 * tree.points.shape[1]
+    l2_bytes = priced * 2 * row + 8.0 * (s_q + s_d) + 4.0
+    hbm_bytes = s_d * row + 8.0 * s_d + 4.0
+    l2_peak = {mb: read_peak_gbs(dev, mb << 20, 20) for mb in (16, 32, 64)}
+    peak = max(l2_peak.values())
+    l2_gbs = l2_bytes * n / (ms * 1e-3) / 1e9
+    hbm_gbs = hbm_bytes * n / (ms * 1e-3) / 1e9
+    return {"bound": "l2", "achieved": l2_gbs, "peak": peak, "unit": "GB/s", "frac": l2_gbs / peak,
+            "peak_kind": "measured (ft_read_probe, L2-resident buffer)",
+            "l2_read_peak_gbs_by_buffer_mib": {str(k): v for k, v in l2_peak.items()},
+            "kernel": "k_flowtree_persistent", "kernel_ms": ms, "pairs": n, "pairs_per_s": n / (ms * 1e-3),
+            "priced_pairs_per_pair": priced, "support_items_per_pair": s_q + s_d, "bytes_per_pair": l2_bytes,
+            "hbm_view": {"bytes_per_pair": hbm_bytes, "achieved": hbm_gbs, "peak": pk["hbm_gbs"],
+                         "frac": hbm_gbs / pk["hbm_gbs"], "peak_kind": pk_kind}}
 
 
 def scan_roofline(tree, Q, D, pk, pk_kind):

@@ -376,6 +376,19 @@ size_t ft_topk_f32_workspace_size(int64_t n_rows, int64_t n_cols);
 ft_status ft_topk_f32(const float* values_dev, int64_t n_rows, int64_t n_cols, int32_t k, void* workspace,
                       size_t ws_bytes, int32_t* ids_out_dev, float* vals_out_dev, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Read-bandwidth probe (measurement utility, not part of the method): the
+ * measured peak that the row-gathering kernels' L2 roofline divides by.
+ * Every SM reads buf_dev[0 .. bytes) `passes` times with independent
+ * 16-byte loads that bypass L1; a buffer that fits in L2 (after one warm
+ * pass) measures L2 read bandwidth, a larger one HBM.  The XOR of all
+ * loaded 32-bit words (passes even: 0) is XOR-ed into *sink_dev, so the
+ * loads cannot be elided.  buf_dev 16-byte aligned, bytes a multiple of
+ * 16 (>= 16), passes >= 1, else FT_EINVAL.  Asynchronous on stream; the
+ * caller times it with events.
+ * ------------------------------------------------------------------------ */
+ft_status ft_read_probe(const void* buf_dev, size_t bytes, int32_t passes, uint32_t* sink_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -82,6 +82,7 @@ SIGNATURES = {
     "ft_knn_exact": (i32, [vp, vp, vp, vp, i32, i32, i32, vp, sz, vp, vp, vp]),
     "ft_topk_f32_workspace_size": (sz, [i64, i64]),
     "ft_topk_f32": (i32, [vp, i64, i64, i32, vp, sz, vp, vp, vp]),
+    "ft_read_probe": (i32, [vp, sz, i32, vp, vp]),
     "ft_flowtree_batch_static": (i32, [vp, vp, vp, vp, vp, vp, i64, vp, vp]),
 }
 

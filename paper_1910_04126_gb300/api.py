@@ -411,6 +411,14 @@ def topk_f32(values: torch.Tensor, k: int, ids: Optional[torch.Tensor] = None,
     return ids, vals
 
 
+def read_probe(buf: torch.Tensor, passes: int, sink: torch.Tensor, stream=None) -> None:
+    """Read buf `passes` times from every SM, bypassing L1 (ft_read_probe): the measured read-bandwidth peak
+    of the L2 roofline.  buf: contiguous device tensor (16-byte aligned, size a multiple of 16 bytes);
+    sink: one int32/uint32 device word."""
+    check(_ffi.load().ft_read_probe(_ptr(buf), buf.numel() * buf.element_size(), passes, _ptr(sink),
+                                    _stream(stream)), "ft_read_probe")
+
+
 class FlowtreeFunction(torch.autograd.Function):
     """Flowtree values of a batch of pairs, differentiable in the vocabulary rows.
 
