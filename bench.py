@@ -754,7 +754,7 @@ def text_flowtree_roofline(tree, Q, D, q_h, db_h, k1, dev, pk, pk_kind):
     timed alone).  Algorithmic bytes per pair: two 4d-byte rows per priced (distinct-point) matched pair
     + 8 B per support item + 4 B out, all through L2 (the query's rows are shared by its k1 candidates);
     the HBM view counts the candidate side once: its rows, supports and the output.  The L2 peak is
-    ft_read_probe over buffers that fit in L2 (the best of 16, 32 and 64 MiB); the priced pairs per pair
+    ft_read_probe over buffers that fit in L2 (the best of 32, 64 and 96 MiB); the priced pairs per pair
     come from the saved flows of the first 20 queries' candidates."""
     import torch
     from paper_1910_04126_gb300 import api
@@ -786,7 +786,7 @@ def text_flowtree_roofline(tree, Q, D, q_h, db_h, k1, dev, pk, pk_kind):
     row = 4.0 * tree.points.shape[1]
     l2_bytes = priced * 2 * row + 8.0 * (s_q + s_d) + 4.0
     hbm_bytes = s_d * row + 8.0 * s_d + 4.0
-    l2_peak = {mb: read_peak_gbs(dev, mb << 20, 20) for mb in (16, 32, 64)}
+    l2_peak = {mb: read_peak_gbs(dev, mb << 20, 50) for mb in (32, 64, 96)}
     peak = max(l2_peak.values())
     l2_gbs = l2_bytes * n / (ms * 1e-3) / 1e9
     hbm_gbs = hbm_bytes * n / (ms * 1e-3) / 1e9

@@ -11,7 +11,7 @@
 namespace {
 
 constexpr int PROBE_THREADS = 256;
-constexpr int PROBE_UNROLL = 4;
+constexpr int PROBE_UNROLL = 8;
 
 __global__ void __launch_bounds__(PROBE_THREADS) k_read_probe(const uint4* __restrict__ p, int64_t n16, int passes,
                                                              unsigned int* __restrict__ sink) {
