@@ -73,6 +73,10 @@ def parse():
     ap.add_argument("--profile-exact", nargs=2, type=int, metavar=("N_Q", "PER_Q"),
                     help="only run exact W1 on N_Q text-shaped queries x PER_Q random documents of 20,000 "
                          "(vocabulary 100,000 x 300) three times (a case for ncu); no timing")
+    ap.add_argument("--profile-text", type=int, metavar="N_Q",
+                    help="only run the Flowtree launch of the text pipeline (N_Q queries x their 1,000 quadtree "
+                         "candidates of 100,000 documents, vocabulary 100,000 x 300, launch configuration from "
+                         "--config) three times (a case for ncu); no timing")
     ap.add_argument("--profile-backward", type=int, metavar="N_PAIRS",
                     help="only run forward (flows saved) + backward on N_PAIRS pairs of the differentiation workload "
                          "(vocabulary 30,000 x 300) three times (a case for ncu); no timing")
@@ -130,6 +134,23 @@ def profile_exact(args):
         api.exact_w1(tree, tree.points, Q, D, pa, pb, workspace=ws)
     torch.cuda.synchronize()
     print("profile exact done: %d pairs, status %d" % (n_q * per_q, tree.status()))
+
+
+def profile_text(args):
+    import torch
+    from paper_1910_04126_gb300 import api, synth
+    n_q, k1 = args.profile_text, 1000
+    vocab = synth.mixture_vocab(100000, 300, 1000, 0.3, 300)
+    db, q = synth.zipf_docs(100000, 100000, 302), synth.zipf_docs(100000, n_q, 303)
+    tree = api.Tree(torch.as_tensor(vocab, device="cuda"), LEVELS, synth.random_shift(300, 301))
+    tree.set_config(*[int(x) for x in args.config.split(",")])
+    D, Q = api.Docs.from_csr(tree, db), api.Docs.from_csr(tree, q)
+    cand = api.quadtree_scan(tree, Q, D, k1).reshape(-1)
+    pa = torch.arange(n_q, dtype=torch.int32, device="cuda").repeat_interleave(k1)
+    for _ in range(3):
+        api.flowtree_batch(tree, tree.points, Q, D, pa, cand)
+    torch.cuda.synchronize()
+    print("profile text done: %d pairs, config %s, status %d" % (n_q * k1, args.config, tree.status()))
 
 
 def profile_backward(args):
@@ -309,6 +330,9 @@ def main():
         return
     if args.profile_backward:
         profile_backward(args)
+        return
+    if args.profile_text:
+        profile_text(args)
         return
 
     import torch
