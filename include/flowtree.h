@@ -160,7 +160,9 @@ ft_status ft_docs_export(const ft_docs* d, int64_t* sup_ptr_host, uint32_t* sup_
  * Flowtree estimate, batched (Sec. 3; greedy flow of App. A.1).
  *
  * For pair i, cost_out_dev[i] = sum over tree-flow pairs (x, y) of
- * f(x, y) / 2^24 * ||vocab[x] - vocab[y]||_2  (FP32 output, FP64 sums).
+ * f(x, y) / 2^24 * ||vocab[x] - vocab[y]||_2: exact integer flows, FP32
+ * distances, per-lane Neumaier-compensated FP32 sums added across the warp
+ * (within 1e-5 relative of the FP64 definition), FP32 output.
  * Pair i is (document pair_a_dev[i] of a, document pair_b_dev[i] of b).  If
  * both pair arrays are NULL the batch is the cross product: pair
  * i = qa * nb + jb for qa < na(a), jb < nb(b), and n_pairs must equal
