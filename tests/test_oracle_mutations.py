@@ -33,6 +33,16 @@ MUTATIONS = {
     "drop_nu_leftover": ("for (; j < nl.nu.size(); ++j) pe.second.nu.push_back(nl.nu[j]);", ";"),
     # total weight taken as the number of entries (uniform assumption)
     "uniform_total": ("total += double(w);", "total += 1.0;"),
+    # adjoint: the nu endpoint moved with the same sign as the mu endpoint
+    "grad_sign_nu": ("grad[size_t(q) * d + c] -= coef * diff;", "grad[size_t(q) * d + c] += coef * diff;"),
+    # adjoint: the unit direction not normalised by the distance
+    "grad_no_normalise": ("double coef = grad_cost[i] * (double(e.f) / double(kMassOne)) / dist;",
+                          "double coef = grad_cost[i] * (double(e.f) / double(kMassOne));"),
+    # exact W1: successive shortest paths without the potential update
+    "mcf_no_potentials": ("if (dist[v] < INF) pot[v] += dist[v];", "if (dist[v] < INF) pot[v] += 0.0;"),
+    # Mean: unweighted centroid of the support instead of the mass-weighted one
+    "mean_unweighted": ("for (int64_t i = 0; i < na; ++i) ca += double(ma[i]) / double(kMassOne) * double(vocab[size_t(pa[i]) * d + t]);",
+                        "for (int64_t i = 0; i < na; ++i) ca += 1.0 / double(na) * double(vocab[size_t(pa[i]) * d + t]);"),
 }
 
 EXTRA = {
