@@ -74,7 +74,7 @@ typedef struct ft_tree ft_tree;   /* quadtree over the ground points          */
 typedef struct ft_docs ft_docs;   /* a set of distributions on the tree       */
 typedef struct ft_flows ft_flows; /* saved tree flows of a batch of pairs     */
 
-/* Limits of this build. */
+/* Compile-time limits of the library. */
 #define FT_MAX_LEVELS 14          /* L <= 14                                  */
 #define FT_MAX_SUPPORT 16383      /* distinct points per distribution (a merged
                                      pair's positions then fit 15 bits)        */
