@@ -41,3 +41,46 @@ def test_library_exports_every_declared_symbol():
 def test_binding_signatures_cover_the_header():
     from paper_1910_04126_gb300 import _ffi
     assert set(declared_functions()) <= set(_ffi.SIGNATURES)
+
+
+def _null_args(argtypes):
+    import ctypes as C
+    out = []
+    for a in argtypes:
+        if a is None or a is C.c_void_p or a is C.c_char_p or (isinstance(a, type) and issubclass(a, C._Pointer)):
+            out.append(None)
+        else:
+            out.append(a(0))
+    return out
+
+
+def test_entry_points_reject_null_handles_before_touching_the_gpu():
+    # Every status-returning entry point validates its handles and pointers on
+    # the host first: called with NULL / zero arguments (here, on a machine
+    # without a GPU) each returns FT_EINVAL, and every *_workspace_size returns
+    # 0, without a CUDA call.
+    from paper_1910_04126_gb300 import _ffi
+    lib = _ffi.load()
+    status_fns, size_fns = [], []
+    for name in declared_functions():
+        res, args = _ffi.SIGNATURES[name]
+        if res is None or name == "ft_status_string":
+            continue
+        fn = getattr(lib, name)
+        r = fn(*_null_args(fn.argtypes or []))
+        if name.endswith("_workspace_size"):
+            size_fns.append(name)
+            assert r == 0, name
+        else:
+            status_fns.append(name)
+            assert r == -1, (name, r)  # FT_EINVAL
+    assert "ft_flowtree_batch" in status_fns and "ft_knn" in status_fns and "ft_read_probe" in status_fns
+    assert "ft_flowtree_backward_workspace_size" in size_fns
+
+
+def test_status_strings_name_every_code():
+    from paper_1910_04126_gb300 import _ffi
+    lib = _ffi.load()
+    for code, name in _ffi.STATUS.items():
+        assert lib.ft_status_string(code).decode().split(":")[0] == name
+    assert lib.ft_status_string(-99).decode() == "unknown ft_status"
