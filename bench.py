@@ -281,6 +281,22 @@ def oracle_rate(pts, shift, db, q, target_s: float, n_threads: int, seed: int = 
         n = int(min(n * max(2.0, 1.2 * target_s / max(dt, 1e-3)), 1 << 24))
 
 
+def host_cpu() -> dict:
+    """The host CPU the oracle ran on: nproc, machine, and lscpu's model name and sockets when available."""
+    import platform
+    import subprocess
+    info = {"nproc": os.cpu_count() or 1, "machine": platform.machine()}
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            key, _, val = line.partition(":")
+            if key.strip() in ("Model name", "Socket(s)", "Core(s) per socket", "Thread(s) per core"):
+                info[key.strip().lower().replace(" ", "_").replace("(s)", "s")] = val.strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return info
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -301,7 +317,7 @@ def run_reference(args, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sample / value,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "sample": "random (query, db) pairs of the workload"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "host": host_cpu(),
                          "sample": "%d random pairs per step of the %s workload" % (sample, "quick" if args.quick else "full")},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -664,7 +680,7 @@ def extras(args, tree, D, Q, q_h, db_h, pts, shift, batched_value, dev, pk, pk_k
     r_1, n_1, dt_1 = oracle_rate(pts, shift, db_h, q_h, 3.0 if not args.quick else 0.5, 1, seed=2)
     out["cpu_baseline"] = {"value": r_n, "unit": UNIT, "cores": cores, "kind": "oracle",
                            "sample": "%d random (query, db) pairs of the image workload, %.1f s" % (n_n, dt_n),
-                           "single_thread": {"value": r_1, "sample_pairs": n_1}}
+                           "single_thread": {"value": r_1, "sample_pairs": n_1}, "host": host_cpu()}
     out["roofline_hbm"] = hbm_roofline(q_h, db_h, batched_value, pk, pk_kind)
     return out
 
