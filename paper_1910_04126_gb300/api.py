@@ -106,6 +106,22 @@ class Tree:
         cfg = _ffi.FlowtreeConfig(warps_per_cta, stage_items, algo, stage_tables)
         check(_ffi.load().ft_flowtree_set_config(self._h, C.byref(cfg)), "ft_flowtree_set_config")
 
+    # -- checkpoint / resume ---------------------------------------------------
+    # The build is deterministic in (points, levels, shift), so a saved index
+    # is those inputs plus the launch configuration; loading rebuilds the same
+    # tree bit for bit (the shift is the realised one, also when it was drawn
+    # from a seed).
+    def save(self, path) -> None:
+        np.savez(path, points=self.points.cpu().numpy(), levels=np.int64(self.levels), shift=self.export()[3],
+                 config=np.asarray(self.get_config(), np.int64))
+
+    @classmethod
+    def load(cls, path, device="cuda", stream=None) -> "Tree":
+        z = np.load(path)
+        t = cls(torch.as_tensor(z["points"], device=device), int(z["levels"]), z["shift"], stream=stream)
+        t.set_config(*(int(x) for x in z["config"]))
+        return t
+
 
 class Docs:
     """Distributions on the tree (ft_embed_docs): rank-sorted supports, 2^24 masses."""
@@ -127,6 +143,16 @@ class Docs:
     @classmethod
     def from_csr(cls, tree: Tree, docs, stream=None) -> "Docs":
         return cls(tree, docs.row_ptr, docs.word, docs.weight, stream)
+
+    def save(self, path) -> None:
+        """The CSR input (the embedding is rebuilt from it deterministically on load)."""
+        np.savez(path, row_ptr=self.row_ptr.cpu().numpy(), word=self.word.cpu().numpy(),
+                 weight=self.weight.cpu().numpy())
+
+    @classmethod
+    def load(cls, tree: Tree, path, stream=None) -> "Docs":
+        z = np.load(path)
+        return cls(tree, z["row_ptr"], z["word"], z["weight"], stream)
 
     def __del__(self):
         h = getattr(self, "_h", None)

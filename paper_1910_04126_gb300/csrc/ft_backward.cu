@@ -420,6 +420,7 @@ extern "C" size_t ft_flowtree_backward_workspace_size(const ft_tree* t, const ft
 extern "C" ft_status ft_flowtree_backward(const ft_tree* t, const ft_docs* a, const ft_docs* b, const ft_flows* flows,
                                           const float* vocab_dev, const float* grad_cost_dev, float* grad_vocab_dev,
                                           void* workspace, size_t ws_bytes, void* stream) {
+    FtRange nvtx_range("ft_flowtree_backward");
     if (!t || !a || !b || !flows || !vocab_dev || !grad_cost_dev || !grad_vocab_dev) return FT_EINVAL;
     if (a->tree != t || b->tree != t) return FT_EINVAL;
     if (flows->cross && flows->nb_cross != b->n_docs) return FT_EINVAL;

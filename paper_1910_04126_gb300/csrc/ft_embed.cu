@@ -493,6 +493,7 @@ ft_status embed(const ft_tree* t, const int64_t* row_ptr, const int32_t* word, c
 
 extern "C" ft_status ft_embed_docs(const ft_tree* t, const int64_t* row_ptr_dev, const int32_t* word_dev,
                                    const float* weight_dev, int64_t n_docs, void* stream, ft_docs** out) {
+    FtRange nvtx_range("ft_embed_docs");
     if (!out) return FT_EINVAL;
     *out = nullptr;
     if (!t || !row_ptr_dev || !word_dev || !weight_dev || n_docs < 1 || n_docs >= (int64_t(1) << 31)) return FT_EINVAL;

@@ -401,6 +401,7 @@ extern "C" size_t ft_exact_w1_workspace_size(const ft_docs* a, const ft_docs* b,
 extern "C" ft_status ft_exact_w1_batch(const float* vocab_dev, const ft_docs* a, const ft_docs* b,
                                        const int32_t* pair_a_dev, const int32_t* pair_b_dev, int64_t n_pairs,
                                        float* cost_out_dev, void* workspace, size_t ws_bytes, void* stream) {
+    FtRange nvtx_range("ft_exact_w1_batch");
     FT_TRY(check_exact(vocab_dev, a, b, pair_a_dev, pair_b_dev, n_pairs, cost_out_dev));
     if (n_pairs == 0) return FT_OK;
     ExactPlan p;

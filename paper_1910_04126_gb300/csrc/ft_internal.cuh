@@ -1,6 +1,7 @@
 // Internal definitions shared by the CUDA translation units of libflowtree.
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -118,6 +119,15 @@ struct WsCarver {
         off += count * sizeof(T);
         return p;
     }
+};
+
+// NVTX range over a host entry point: names the call in a profiler's
+// timeline (a no-op unless a profiling tool is attached).
+struct FtRange {
+    explicit FtRange(const char* name) { nvtxRangePushA(name); }
+    ~FtRange() { nvtxRangePop(); }
+    FtRange(const FtRange&) = delete;
+    FtRange& operator=(const FtRange&) = delete;
 };
 
 // ---------------------------------------------------------------------------

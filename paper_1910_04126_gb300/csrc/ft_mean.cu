@@ -117,6 +117,7 @@ extern "C" size_t ft_mean_scan_workspace_size(const ft_docs* queries, const ft_d
 extern "C" ft_status ft_mean_scan(const float* vocab_dev, const ft_docs* queries, const ft_docs* db, int32_t k1,
                                   void* workspace, size_t ws_bytes, int32_t* cand_ids_out_dev,
                                   float* cand_dist_out_dev, void* stream) {
+    FtRange nvtx_range("ft_mean_scan");
     FT_TRY(check_mean(vocab_dev, queries, db, k1));
     if (!cand_ids_out_dev || !cand_dist_out_dev) return FT_EINVAL;
     if (!workspace || ws_bytes < mean_layout(queries, db, nullptr, nullptr)) return FT_EWORKSPACE;

@@ -528,6 +528,7 @@ extern "C" size_t ft_quadtree_scan_workspace_size(const ft_tree* t, const ft_doc
 extern "C" ft_status ft_quadtree_scan(const ft_tree* t, const ft_docs* queries, const ft_docs* db, int32_t k1,
                                       void* workspace, size_t ws_bytes, int32_t* cand_ids_out_dev,
                                       int64_t* cand_l1_out_dev, void* stream) {
+    FtRange nvtx_range("ft_quadtree_scan");
     FT_TRY(check_scan(t, queries, db, k1));
     if (!cand_ids_out_dev) return FT_EINVAL;
     if (!workspace || ws_bytes < scan_layout(queries, db, nullptr, nullptr)) return FT_EWORKSPACE;
@@ -543,6 +544,7 @@ extern "C" ft_status ft_quadtree_scan(const ft_tree* t, const ft_docs* queries, 
 
 extern "C" ft_status ft_quadtree_l1_dense(const ft_tree* t, const ft_docs* queries, const ft_docs* db,
                                           int64_t* l1_all_out_dev, void* stream) {
+    FtRange nvtx_range("ft_quadtree_l1_dense");
     FT_TRY(check_scan(t, queries, db, 1));
     if (!l1_all_out_dev) return FT_EINVAL;
     return launch_scan(t, queries, db, nullptr, l1_all_out_dev, static_cast<cudaStream_t>(stream));
@@ -617,6 +619,7 @@ extern "C" size_t ft_knn_workspace_size(const ft_tree* t, const ft_docs* db, con
 extern "C" ft_status ft_knn(const ft_tree* t, const float* vocab_dev, const ft_docs* db, const ft_docs* queries,
                             int32_t k1, int32_t k, void* workspace, size_t ws_bytes, int32_t* ids_out_dev,
                             float* dist_out_dev, void* stream) {
+    FtRange nvtx_range("ft_knn");
     FT_TRY(check_scan(t, queries, db, k1));
     if (!vocab_dev || !ids_out_dev || !dist_out_dev || k < 1 || k > k1) return FT_EINVAL;
     if (!workspace || ws_bytes < knn_layout(t, db, queries, k1, nullptr, nullptr)) return FT_EWORKSPACE;
@@ -674,6 +677,7 @@ extern "C" size_t ft_knn_exact_workspace_size(const ft_tree* t, const ft_docs* d
 extern "C" ft_status ft_knn_exact(const ft_tree* t, const float* vocab_dev, const ft_docs* db, const ft_docs* queries,
                                   int32_t k1, int32_t k2, int32_t k, void* workspace, size_t ws_bytes,
                                   int32_t* ids_out_dev, float* dist_out_dev, void* stream) {
+    FtRange nvtx_range("ft_knn_exact");
     FT_TRY(check_scan(t, queries, db, k1));
     if (!vocab_dev || !ids_out_dev || !dist_out_dev || k < 1 || k > k2 || k2 > k1) return FT_EINVAL;
     if (ft_exact_w1_workspace_size(queries, db, queries->n_docs * int64_t(k2)) == 0) return FT_EUNSUPPORTED;
@@ -710,6 +714,7 @@ extern "C" size_t ft_topk_f32_workspace_size(int64_t n_rows, int64_t n_cols) {
 
 extern "C" ft_status ft_topk_f32(const float* values_dev, int64_t n_rows, int64_t n_cols, int32_t k, void* workspace,
                                  size_t ws_bytes, int32_t* ids_out_dev, float* vals_out_dev, void* stream) {
+    FtRange nvtx_range("ft_topk_f32");
     if (!values_dev || !ids_out_dev || !vals_out_dev || n_rows < 1 || n_cols < 1 || k < 1 || k > MAX_K1 ||
         int64_t(k) > n_cols || n_cols >= (int64_t(1) << 32) || n_rows > 0x7FFFFFFF)
         return FT_EINVAL;

@@ -54,6 +54,7 @@ ft_status static_scratch(void** out) {
 extern "C" ft_status ft_flowtree_batch_static(const ft_tree* t, const float* vocab_dev, const ft_docs* a,
                                               const ft_docs* b, const int32_t* pair_a_dev, const int32_t* pair_b_dev,
                                               int64_t n_pairs, float* cost_out_dev, void* stream) {
+    FtRange nvtx_range("ft_flowtree_batch_static");
     if (!t || !a || !b || !vocab_dev || !cost_out_dev || n_pairs < 0) return FT_EINVAL;
     if (n_pairs == 0) return FT_OK;
     const size_t need = ft_flowtree_batch_workspace_size(t, a, b, n_pairs);

@@ -335,6 +335,7 @@ ft_status build(const float* pts, int64_t n, int d, int L, const uint64_t* shift
 
 extern "C" ft_status ft_build_quadtree(const float* points_dev, int64_t n_points, int32_t dim, int32_t levels,
                                        const uint64_t* shift_host, uint64_t seed, void* stream, ft_tree** out) {
+    FtRange nvtx_range("ft_build_quadtree");
     if (!out) return FT_EINVAL;
     *out = nullptr;
     if (!points_dev || n_points < 1 || n_points >= (int64_t(1) << 24) || dim < 1 || levels < 1 ||
