@@ -191,12 +191,21 @@ ft_status ft_flowtree_batch(const ft_tree* t, const float* vocab_dev, const ft_d
  * (no saved flows); the workspace comes from a fixed device array of
  * FT_STATIC_SCRATCH_BYTES compiled into the library, held by every GPU that
  * loads it until the library is unloaded.  Calls no cudaMalloc/cudaFree.
- *   - Limit: a batch whose ft_flowtree_batch_workspace_size() exceeds
- *     FT_STATIC_SCRATCH_BYTES is rejected with FT_ETOOBIG before any launch
- *     (explicit pair lists up to about 1.2 million pairs; cross products whose
- *     pairs fit the on-chip staging).
+ *   - Limit: a batch whose launch needs more workspace than
+ *     FT_STATIC_SCRATCH_BYTES is rejected with FT_ETOOBIG before any launch.
+ *     The need is that of the launch this call makes: an explicit pair list
+ *     needs about 13 bytes per pair for its longest-first order (up to about
+ *     1.2 million pairs); a cross product needs only the work-queue counter,
+ *     whatever its size, unless the FT_ALGO_WARP form has to spill pairs
+ *     longer than its on-chip staging to per-warp overflow space.  Planning
+ *     errors (FT_EUNSUPPORTED for a configuration the device cannot run) are
+ *     returned as ft_flowtree_batch would return them.
  *   - The first call on a device (with that device current) looks up the
  *     array's device address; make that first call before any stream capture.
+ *     The address is cached per device ordinal for the life of the process:
+ *     it does not survive cudaDeviceReset (or any other teardown of the
+ *     device's primary context), after which this entry point must not be
+ *     called again in the same process.
  *   - Every call shares the array, which keeps the previous call's contents
  *     (what must start at zero is cleared by each call): calls that overlap on
  *     the GPU race and give undefined results; serialise them on one stream. */
@@ -213,11 +222,16 @@ ft_status ft_flowtree_plain(const ft_tree* t, const float* vocab_dev, const ft_d
 
 /* Launch configuration of ft_flowtree_batch.  0 = default for every field.
  *   algo          : FT_ALGO_AUTO, FT_ALGO_WARP (a warp per pair, level by
- *                   level over the merged supports staged in shared memory)
- *                   or FT_ALGO_THREAD (a thread per pair, one sweep with a
- *                   stack of open tree nodes, its per-position state as bit
- *                   arrays in shared memory; dim <= 8 only).  AUTO = WARP;
- *                   ft_flowtree_autotune picks either.
+ *                   level over the merged supports staged in shared memory,
+ *                   compacted after every depth), FT_ALGO_THREAD (a thread
+ *                   per pair, one sweep with a stack of open tree nodes, its
+ *                   per-position state as bit arrays in shared memory;
+ *                   dim <= 8 only) or FT_ALGO_BLOCKED (a warp per pair, each
+ *                   lane holding a contiguous block of up to 15 merged items
+ *                   in registers: pairs of at most 480 merged items).
+ *                   AUTO = BLOCKED when every pair of the batch can have at
+ *                   most 480 merged items, else WARP; ft_flowtree_autotune
+ *                   picks among all three.
  *   warps_per_cta : warps per CTA (1..8).
  *   stage_items   : merged support items each warp stages on chip (WARP).
  *   stage_tables  : 1 = copy the vocabulary and the LCA table into shared
@@ -229,6 +243,7 @@ ft_status ft_flowtree_plain(const ft_tree* t, const float* vocab_dev, const ft_d
 #define FT_ALGO_AUTO 0
 #define FT_ALGO_WARP 1
 #define FT_ALGO_THREAD 2
+#define FT_ALGO_BLOCKED 3
 typedef struct {
     int32_t warps_per_cta;
     int32_t stage_items;

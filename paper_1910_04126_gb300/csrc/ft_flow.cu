@@ -5,6 +5,7 @@
 #include <cstring>
 
 #include "ft_flow.cuh"
+#include "ft_flow_blocked.cuh"
 #include "ft_flow_thread.cuh"
 
 using namespace ftk;
@@ -13,6 +14,7 @@ namespace {
 
 constexpr int kDefaultWarps = 4;
 constexpr int kMaxStage = 2048;
+constexpr int kBlockedCap = 32 * 31;  // longest pair of the blocked form (31 items per lane)
 
 // A warp per pair, persistent: warps take `grab` consecutive queue entries at
 // a time.  Dynamic shared memory: [tables (if staged)] [one WarpBuf per warp].
@@ -47,6 +49,42 @@ __global__ void __launch_bounds__(256) k_flowtree_persistent(FlowCtx c, int cap,
                 cost = flowtree_pair<MODE, SAVE>(c, sbuf, tb, pair, da, db);
             } else if (c.gscratch && n <= c.gscratch_items) {
                 cost = flowtree_pair<MODE, SAVE>(c, gbuf, tb, pair, da, db);
+            } else {
+                if (lane == 0) ft_flag(c.status, FT_DEV_EOVERFLOW);
+                cost = __int_as_float(0x7fc00000);
+            }
+            if (lane == 0) c.cost_out[pair] = cost;
+        }
+    }
+}
+
+// A warp per pair, register-blocked (ft_flow_blocked.cuh), persistent.
+// Dynamic shared memory: [tables (if staged)] [one BlockedBuf per warp].
+template <int MODE, bool SAVE>
+__global__ void __launch_bounds__(256) k_flowtree_blocked(FlowCtx c, int grab, int cap, int tables_bytes) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int warp = int(threadIdx.x >> 5);
+    const unsigned lane = lane_id();
+    const Tables tb = tables_bytes > 0 ? stage_tables(c, smem) : Tables{c.vocab, c.rmq};
+    const BlockedBuf w = carve_blockedbuf(smem + tables_bytes + size_t(warp) * blockedbuf_bytes(cap), cap);
+    const int64_t n_pairs = c.n_pairs;
+    for (;;) {
+        unsigned long long first = 0;
+        if (lane == 0) first = atomicAdd(reinterpret_cast<unsigned long long*>(c.queue), (unsigned long long)grab);
+        first = __shfl_sync(FULL_MASK, first, 0);
+        if (first >= (unsigned long long)n_pairs) break;
+        const int64_t last = min(int64_t(first) + grab, n_pairs);
+        for (int64_t q = int64_t(first); q < last; ++q) {
+            const int64_t pair = c.order ? int64_t(c.order[q]) : q;
+            int64_t da, db;
+            if (!pair_docs(c, pair, &da, &db)) {
+                if (lane == 0) c.cost_out[pair] = __int_as_float(0x7fc00000);
+                continue;
+            }
+            const int n = int(c.a_ptr[da + 1] - c.a_ptr[da]) + int(c.b_ptr[db + 1] - c.b_ptr[db]);
+            float cost;
+            if (n <= cap) {
+                cost = flowtree_pair_blocked<MODE, SAVE>(c, w, tb, pair, da, db);
             } else {
                 if (lane == 0) ft_flag(c.status, FT_DEV_EOVERFLOW);
                 cost = __int_as_float(0x7fc00000);
@@ -228,6 +266,17 @@ void* persistent_fn() {
     return reinterpret_cast<void*>(&k_flowtree_persistent<MODE, SAVE>);
 }
 
+void* blocked_kernel(int mode, bool save) {
+    switch (mode * 2 + (save ? 1 : 0)) {
+        case 0: return reinterpret_cast<void*>(&k_flowtree_blocked<0, false>);
+        case 1: return reinterpret_cast<void*>(&k_flowtree_blocked<0, true>);
+        case 2: return reinterpret_cast<void*>(&k_flowtree_blocked<1, false>);
+        case 3: return reinterpret_cast<void*>(&k_flowtree_blocked<1, true>);
+        case 4: return reinterpret_cast<void*>(&k_flowtree_blocked<2, false>);
+        default: return reinterpret_cast<void*>(&k_flowtree_blocked<2, true>);
+    }
+}
+
 void* persistent_kernel(int mode, bool save) {
     switch (mode * 2 + (save ? 1 : 0)) {
         case 0: return persistent_fn<0, false>();
@@ -253,7 +302,7 @@ ft_status make_plan(const ft_tree* t, const ft_docs* a, const ft_docs* b, int64_
     const int maxn = round32(std::max(a->max_support + b->max_support, 32));
     p->need_order = explicit_pairs && n_pairs > 1;
     const bool thread_ok = t->dim <= 8 && maxn <= kThreadMaxItems;
-    p->algo = cfg.algo != FT_ALGO_AUTO ? cfg.algo : FT_ALGO_WARP;
+    p->algo = cfg.algo != FT_ALGO_AUTO ? cfg.algo : (maxn <= kBlockedCap ? FT_ALGO_BLOCKED : FT_ALGO_WARP);
     int dev = 0, max_smem = 0, sms = 0;
     FT_CUDA(cudaGetDevice(&dev));
     FT_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
@@ -274,6 +323,17 @@ ft_status make_plan(const ft_tree* t, const ft_docs* a, const ft_docs* b, int64_
         // slice of residual words in the workspace)
         const int64_t need_blocks = (std::max<int64_t>(n_pairs, 1) + p->twarps * 32 - 1) / (p->twarps * 32);
         p->tblocks = int(std::min<int64_t>(int64_t(sms) * bps, need_blocks));
+        return FT_OK;
+    }
+    if (p->algo == FT_ALGO_BLOCKED) {
+        if (maxn > kBlockedCap) return FT_EUNSUPPORTED;
+        p->cap = 32 * ((maxn / 32) | 1);  // an odd number of items per lane
+        p->smem = size_t(p->tables_bytes) + size_t(p->warps) * blockedbuf_bytes(p->cap);
+        if (p->smem > size_t(max_smem)) return FT_EUNSUPPORTED;
+        int bps = 0;
+        FT_TRY(ft_prepare_kernel(blocked_kernel(mode, save), p->warps * 32, p->smem, &bps));
+        if (bps < 1) return FT_EUNSUPPORTED;
+        p->blocks = sms * bps;
         return FT_OK;
     }
     int cap = cfg.stage_items > 0 ? round32(cfg.stage_items) : std::min(maxn, 512);
@@ -360,9 +420,14 @@ ft_status launch_warps(const Plan& p, const FlowCtx& c, bool save, cudaStream_t 
     const int64_t n_warps = int64_t(p.blocks) * p.warps;
     int64_t grab = c.n_pairs / (n_warps * 32);
     grab = std::max<int64_t>(1, std::min<int64_t>(grab, 16));
-    void* fn = persistent_kernel(p.mode, save);
     FlowCtx cc = c;
     int cap = p.cap, g = int(grab), tbytes = p.tables_bytes;
+    if (p.algo == FT_ALGO_BLOCKED) {
+        void* args[] = {&cc, &g, &cap, &tbytes};
+        FT_CUDA(cudaLaunchKernel(blocked_kernel(p.mode, save), dim3(p.blocks), dim3(p.warps * 32), args, p.smem, s));
+        return FT_OK;
+    }
+    void* fn = persistent_kernel(p.mode, save);
     void* args[] = {&cc, &cap, &g, &tbytes};
     FT_CUDA(cudaLaunchKernel(fn, dim3(p.blocks), dim3(p.warps * 32), args, p.smem, s));
     return FT_OK;
@@ -443,6 +508,20 @@ void free_flows(ft_flows* f) {
 
 }  // namespace
 
+// Workspace of the launch ft_flowtree_batch would make for these arguments
+// without saved flows (the plan it runs: cross product or explicit pairs, the
+// pricing mode of this vocabulary); the plan's own status on failure.
+ft_status ft_flowtree_batch_need(const ft_tree* t, const float* vocab, const ft_docs* a, const ft_docs* b,
+                                 const int32_t* pa, const int32_t* pb, int64_t n_pairs, size_t* need) {
+    *need = 0;
+    FT_TRY(check_common(t, vocab, a, b, pa, pb, n_pairs, vocab));
+    if (n_pairs == 0) return FT_OK;
+    Plan p;
+    FT_TRY(make_plan(t, a, b, n_pairs, pick_mode(t, vocab), false, pa != nullptr, t->cfg, &p));
+    *need = layout(p, nullptr, nullptr);
+    return FT_OK;
+}
+
 extern "C" size_t ft_flowtree_batch_workspace_size(const ft_tree* t, const ft_docs* a, const ft_docs* b,
                                                    int64_t n_pairs) {
     if (!t || !a || !b || n_pairs < 0) return 0;
@@ -512,6 +591,10 @@ extern "C" ft_status ft_flowtree_autotune(ft_tree* t, const float* vocab_dev, co
         if (cap > maxn || cap > kMaxStage) continue;
         for (int w : warps)
             for (int st : {0, 1}) cands.push_back({w, cap, FT_ALGO_WARP, st});
+    }
+    if (maxn <= kBlockedCap) {
+        for (int w : {2, 3, 4, 6, 8})
+            for (int st : {0, 1}) cands.push_back({w, 0, FT_ALGO_BLOCKED, st});
     }
     if (t->dim <= 8 && maxn <= kThreadMaxItems) {
         // lane per pair: warps per block x item buffer entries per lane

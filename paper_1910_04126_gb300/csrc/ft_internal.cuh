@@ -236,3 +236,8 @@ ft_status ft_sort_perm_by_u32(const uint32_t* keys, uint32_t* perm, int64_t n, i
 // Only byte positions with varying[b] != 0 are sorted on (host array).
 ft_status ft_sort_perm_by_bytes(const uint8_t* keys, int key_bytes, const std::vector<uint8_t>& varying,
                                 uint32_t* perm, int64_t n, void* tmp, cudaStream_t s);
+
+// Workspace bytes of the launch ft_flowtree_batch makes for these arguments
+// without saved flows (ft_flow.cu); returns the planning status.
+ft_status ft_flowtree_batch_need(const ft_tree* t, const float* vocab, const ft_docs* a, const ft_docs* b,
+                                 const int32_t* pa, const int32_t* pb, int64_t n_pairs, size_t* need);

@@ -57,8 +57,10 @@ extern "C" ft_status ft_flowtree_batch_static(const ft_tree* t, const float* voc
     FtRange nvtx_range("ft_flowtree_batch_static");
     if (!t || !a || !b || !vocab_dev || !cost_out_dev || n_pairs < 0) return FT_EINVAL;
     if (n_pairs == 0) return FT_OK;
-    const size_t need = ft_flowtree_batch_workspace_size(t, a, b, n_pairs);
-    if (need == 0) return FT_EINVAL;
+    // the scratch this call's own plan needs (a cross product needs no pair
+    // order, an explicit pair list does); planning errors pass through
+    size_t need = 0;
+    FT_TRY(ft_flowtree_batch_need(t, vocab_dev, a, b, pair_a_dev, pair_b_dev, n_pairs, &need));
     if (need > size_t(FT_STATIC_SCRATCH_BYTES)) return FT_ETOOBIG;
     void* scratch = nullptr;
     FT_TRY(static_scratch(&scratch));

@@ -73,3 +73,23 @@ def test_static_scratch_rejects_batches_beyond_its_size():
     out = torch.empty(n, dtype=torch.float32, device=dev)
     code = _call_static(tree, tree.points, D, D, pa, pa, n, out)
     assert code == -8  # FT_ETOOBIG, refused before any launch
+
+
+def test_static_scratch_large_cross_product():
+    """A cross product far beyond the explicit-pair limit (2.5 million pairs):
+    it needs no pair order, so it fits the fixed scratch and must match the
+    workspace entry point."""
+    dev = torch.device("cuda")
+    pts = np.random.default_rng(0).random((1000, 2)).astype(np.float32)
+    tree = api.Tree(torch.as_tensor(pts, device=dev), 12, synth.random_shift(2, 21))
+    Da = api.Docs.from_csr(tree, synth.uniform_docs(1000, 50, 10, 30, 22))
+    Db = api.Docs.from_csr(tree, synth.uniform_docs(1000, 50000, 10, 30, 23))
+    n = 50 * 50000
+    ref = api.flowtree_batch(tree, tree.points, Da, Db)
+    for _ in range(2):
+        out = torch.full((n,), float("nan"), dtype=torch.float32, device=dev)
+        code = _call_static(tree, tree.points, Da, Db, None, None, n, out)
+        assert code == _ffi.FT_OK, _ffi.STATUS.get(code)
+        torch.cuda.synchronize()
+        torch.testing.assert_close(out, ref, rtol=REL, atol=0)
+    assert tree.status() == 0
