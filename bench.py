@@ -45,6 +45,18 @@ N_DB, N_Q, LEVELS, TOPK = 60000, 1000, 12, 10
 WORKLOAD = ("image-shaped: 28x28 grid ground set, 60,000 db x 1,000 query distributions of 100-200 pixels, "
             "L=12, Flowtree for every query-database pair + top-10 per query")
 ALU_LANES_PER_SM = 128  # FP32/INT32 lanes per SM (4 SMSPs x 32)
+ALGO_NAMES = ["auto", "warp", "thread", "blocked"]  # ft_flowtree_config.algo
+FLOW_KERNEL = {1: "k_flowtree_persistent", 2: "k_flowtree_thread", 3: "k_flowtree_blocked"}
+
+
+def flow_kernel(tree, a, b) -> str:
+    """The Flowtree kernel a batch of (a, b) pairs launches with the tree's configuration."""
+    from paper_1910_04126_gb300 import _ffi
+    algo = tree.get_config()[2]
+    if algo == _ffi.ALGO_AUTO:
+        maxn = ((a.info.max_support + b.info.max_support + 31) // 32) * 32
+        algo = _ffi.ALGO_BLOCKED if maxn <= _ffi.BLOCKED_MAX_ITEMS else _ffi.ALGO_WARP
+    return FLOW_KERNEL[algo]
 
 
 def peaks():
@@ -242,7 +254,7 @@ def make_image(rank: int, quick: bool):
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("ft_flow.cuh", "ft_flow.cu"):
+    for f in ("ft_flow.cuh", "ft_flow_blocked.cuh", "ft_flow.cu"):
         with open(os.path.join(ROOT, "paper_1910_04126_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -453,7 +465,7 @@ def main():
     e2e_value = world * n_pairs / (statistics.mean(e2e_ms) * 1e-3)
 
     pk, pk_kind = peaks()
-    # algorithmic work of the dominant kernel (k_flowtree_persistent), per launch:
+    # algorithmic work of the dominant kernel (the Flowtree launch), per launch:
     # (L+2)(s_mu+s_nu) integer scan steps + (s_mu+s_nu-1)(3d+1) FLOP per pair
     lq = np.diff(q_h.row_ptr).astype(np.float64)
     ld = np.diff(db_h.row_ptr).astype(np.float64)
@@ -473,7 +485,7 @@ def main():
         "config": {"workload": WORKLOAD + (" [quick]" if args.quick else ""), "pairs_per_step_per_gpu": n_pairs,
                    "l2": "flushed (512 MiB write) before every timed step", "parallelism": "weak, %d shard(s)" % world,
                    "launch_config": {"warps_per_cta": tuned[0], "stage_items": tuned[1],
-                                     "algo": ["auto", "warp", "thread"][tuned[2]], "stage_tables": tuned[3],
+                                     "algo": ALGO_NAMES[tuned[2]], "stage_tables": tuned[3],
                                      "picked_by": "ft_flowtree_autotune"}},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": statistics.mean(e2e_ms)},
@@ -482,7 +494,7 @@ def main():
         "clocks": clocks,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": alu_peak / 1e12, "unit": "Tops/s",
                      "frac": achieved / alu_peak, "traffic": traffic,
-                     "kernel": "k_flowtree_persistent", "kernel_ms": kms,
+                     "kernel": flow_kernel(tree, Q, D), "kernel_ms": kms,
                      "peak_basis": "%d SMs x %d lanes x %.0f MHz (%s sm_max_mhz)" % (n_sm, ALU_LANES_PER_SM, sm_clock, pk_kind)},
     }
     if rank == 0 and world == 1 and not args.no_extras:
@@ -833,7 +845,7 @@ def text_flowtree_roofline(tree, Q, D, q_h, db_h, k1, dev, pk, pk_kind):
     return {"bound": "l2", "achieved": l2_gbs, "peak": peak, "unit": "GB/s", "frac": l2_gbs / peak,
             "peak_kind": "measured (ft_read_probe, L2-resident buffer)",
             "l2_read_peak_gbs_by_buffer_mib": {str(k): v for k, v in l2_peak.items()},
-            "kernel": "k_flowtree_persistent", "kernel_ms": ms, "pairs": n, "pairs_per_s": n / (ms * 1e-3),
+            "kernel": flow_kernel(tree, Q, D), "kernel_ms": ms, "pairs": n, "pairs_per_s": n / (ms * 1e-3),
             "priced_pairs_per_pair": priced, "support_items_per_pair": s_q + s_d, "bytes_per_pair": l2_bytes,
             "hbm_view": {"bytes_per_pair": hbm_bytes, "achieved": hbm_gbs, "peak": pk["hbm_gbs"],
                          "frac": hbm_gbs / pk["hbm_gbs"], "peak_kind": pk_kind}}

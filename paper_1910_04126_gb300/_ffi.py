@@ -31,7 +31,8 @@ class DocsInfo(C.Structure):
                 ("n_embed", C.c_int64)]
 
 
-ALGO_AUTO, ALGO_WARP, ALGO_THREAD = 0, 1, 2
+ALGO_AUTO, ALGO_WARP, ALGO_THREAD, ALGO_BLOCKED = 0, 1, 2, 3
+BLOCKED_MAX_ITEMS = 992  # longest merged pair of the blocked form (31 items per lane)
 
 
 class FlowtreeConfig(C.Structure):

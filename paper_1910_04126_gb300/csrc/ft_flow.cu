@@ -60,13 +60,15 @@ __global__ void __launch_bounds__(256) k_flowtree_persistent(FlowCtx c, int cap,
 
 // A warp per pair, register-blocked (ft_flow_blocked.cuh), persistent.
 // Dynamic shared memory: [tables (if staged)] [one BlockedBuf per warp].
-template <int MODE, bool SAVE>
+template <int MODE, bool SAVE, bool PT16>
 __global__ void __launch_bounds__(256) k_flowtree_blocked(FlowCtx c, int grab, int cap, int tables_bytes) {
     extern __shared__ __align__(16) uint8_t smem[];
     const int warp = int(threadIdx.x >> 5);
     const unsigned lane = lane_id();
     const Tables tb = tables_bytes > 0 ? stage_tables(c, smem) : Tables{c.vocab, c.rmq};
-    const BlockedBuf w = carve_blockedbuf(smem + tables_bytes + size_t(warp) * blockedbuf_bytes(cap), cap);
+    const BlockedBuf w =
+        carve_blockedbuf(smem + tables_bytes + size_t(warp) * blockedbuf_bytes(cap, PT16, blocked_has_meta(PT16, SAVE)),
+                         cap, PT16, blocked_has_meta(PT16, SAVE));
     const int64_t n_pairs = c.n_pairs;
     for (;;) {
         unsigned long long first = 0;
@@ -84,7 +86,7 @@ __global__ void __launch_bounds__(256) k_flowtree_blocked(FlowCtx c, int grab, i
             const int n = int(c.a_ptr[da + 1] - c.a_ptr[da]) + int(c.b_ptr[db + 1] - c.b_ptr[db]);
             float cost;
             if (n <= cap) {
-                cost = flowtree_pair_blocked<MODE, SAVE>(c, w, tb, pair, da, db);
+                cost = flowtree_pair_blocked<MODE, SAVE, PT16>(c, w, tb, pair, da, db);
             } else {
                 if (lane == 0) ft_flag(c.status, FT_DEV_EOVERFLOW);
                 cost = __int_as_float(0x7fc00000);
@@ -239,6 +241,7 @@ struct Plan {
     bool need_order = false;
     int64_t n_pairs = 0;
     int tables_bytes = 0;  // vocabulary + LCA table staged in shared memory (0 = read from global)
+    void* kernel = nullptr;  // blocked form: the instantiation to launch
     // thread algorithm: the lane-per-pair launch; cap, warps, blocks, smem
     // above then describe the warp-per-pair launch for its overflow pairs
     int tw = 0;            // words per bit array of a lane (positions up to the longest pair)
@@ -266,15 +269,23 @@ void* persistent_fn() {
     return reinterpret_cast<void*>(&k_flowtree_persistent<MODE, SAVE>);
 }
 
-void* blocked_kernel(int mode, bool save) {
+template <bool PT16>
+void* blocked_fn(int mode, bool save) {
     switch (mode * 2 + (save ? 1 : 0)) {
-        case 0: return reinterpret_cast<void*>(&k_flowtree_blocked<0, false>);
-        case 1: return reinterpret_cast<void*>(&k_flowtree_blocked<0, true>);
-        case 2: return reinterpret_cast<void*>(&k_flowtree_blocked<1, false>);
-        case 3: return reinterpret_cast<void*>(&k_flowtree_blocked<1, true>);
-        case 4: return reinterpret_cast<void*>(&k_flowtree_blocked<2, false>);
-        default: return reinterpret_cast<void*>(&k_flowtree_blocked<2, true>);
+        case 0: return reinterpret_cast<void*>(&k_flowtree_blocked<0, false, PT16>);
+        case 1: return reinterpret_cast<void*>(&k_flowtree_blocked<0, true, PT16>);
+        case 2: return reinterpret_cast<void*>(&k_flowtree_blocked<1, false, PT16>);
+        case 3: return reinterpret_cast<void*>(&k_flowtree_blocked<1, true, PT16>);
+        case 4: return reinterpret_cast<void*>(&k_flowtree_blocked<2, false, PT16>);
+        default: return reinterpret_cast<void*>(&k_flowtree_blocked<2, true, PT16>);
     }
+}
+
+// 16-bit point ids per merged position when the ground set allows
+bool blocked_pt16(const ft_tree* t) { return t->n <= 65536; }
+
+void* blocked_kernel(const ft_tree* t, int mode, bool save) {
+    return blocked_pt16(t) ? blocked_fn<true>(mode, save) : blocked_fn<false>(mode, save);
 }
 
 void* persistent_kernel(int mode, bool save) {
@@ -328,10 +339,12 @@ ft_status make_plan(const ft_tree* t, const ft_docs* a, const ft_docs* b, int64_
     if (p->algo == FT_ALGO_BLOCKED) {
         if (maxn > kBlockedCap) return FT_EUNSUPPORTED;
         p->cap = 32 * ((maxn / 32) | 1);  // an odd number of items per lane
-        p->smem = size_t(p->tables_bytes) + size_t(p->warps) * blockedbuf_bytes(p->cap);
+        p->smem = size_t(p->tables_bytes) +
+                  size_t(p->warps) * blockedbuf_bytes(p->cap, blocked_pt16(t), blocked_has_meta(blocked_pt16(t), save));
         if (p->smem > size_t(max_smem)) return FT_EUNSUPPORTED;
         int bps = 0;
-        FT_TRY(ft_prepare_kernel(blocked_kernel(mode, save), p->warps * 32, p->smem, &bps));
+        p->kernel = blocked_kernel(t, mode, save);
+        FT_TRY(ft_prepare_kernel(p->kernel, p->warps * 32, p->smem, &bps));
         if (bps < 1) return FT_EUNSUPPORTED;
         p->blocks = sms * bps;
         return FT_OK;
@@ -424,7 +437,7 @@ ft_status launch_warps(const Plan& p, const FlowCtx& c, bool save, cudaStream_t 
     int cap = p.cap, g = int(grab), tbytes = p.tables_bytes;
     if (p.algo == FT_ALGO_BLOCKED) {
         void* args[] = {&cc, &g, &cap, &tbytes};
-        FT_CUDA(cudaLaunchKernel(blocked_kernel(p.mode, save), dim3(p.blocks), dim3(p.warps * 32), args, p.smem, s));
+        FT_CUDA(cudaLaunchKernel(p.kernel, dim3(p.blocks), dim3(p.warps * 32), args, p.smem, s));
         return FT_OK;
     }
     void* fn = persistent_kernel(p.mode, save);

@@ -11,6 +11,9 @@
 //   * the items that match something at a depth are listed (by ballot, in
 //     the second walk) and then processed 32 at a time, so the partner
 //     searches run with every lane busy;
+//   * the ground-point ids of the matched pairs come from shared memory: per
+//     merged position (16-bit, moved with the items) for ground sets of at
+//     most 65,536 points, else per support item;
 //   * after the point level and after every depth the survivors are
 //     compacted into a new blocked layout (the LCA depth between two
 //     survivors is the minimum over the dropped span), which also yields the
@@ -40,17 +43,23 @@ struct BlockedBuf {
     uint32_t* it;     // [cap] items (it_make)
     uint32_t* list;   // [cap] items that match at the current depth: position | run head << 16
     uint32_t* M;      // [cap] at run heads: the run's matched mass min(mu total, nu total)
-    uint32_t* qe;     // [64] queued pairs: mu index | nu index << 16
+    uint32_t* qe;     // [64] queued pairs: (PT16) mu point | nu point << 16, else mu index | nu index << 16
     uint32_t* qf;     // [64] their flow
-    uint16_t* NX;     // [cap] at run heads: position of the next run head
-    uint16_t* meta;   // [cap] bit 15 side (0 mu, 1 nu), bits 0..14 index in its support
+    uint32_t* wd;     // (not PT16) [cap] ground-point ids of the two supports (mu items, then nu items)
+    uint16_t* meta;   // (with meta) [cap] bit 15 side (0 mu, 1 nu), bits 0..14 index in its support
+    uint16_t* pt;     // (PT16) [cap] ground-point id of the item at each position
 };
 
-__host__ __device__ inline size_t blockedbuf_bytes(int cap) {
-    return (size_t(cap + 1) * 8 + size_t(cap) * 16 + 512 + 15) & ~size_t(15);
+// PT16: ground sets of at most 65,536 points (16-bit point ids per position).
+// The support indices (meta) are kept when flows are saved or the pricing
+// resolves point ids through them (not PT16).
+__host__ __device__ inline bool blocked_has_meta(bool pt16, bool save) { return save || !pt16; }
+
+__host__ __device__ inline size_t blockedbuf_bytes(int cap, bool pt16, bool meta) {
+    return (size_t(cap + 1) * 8 + size_t(cap) * (12 + (meta ? 2 : 0) + (pt16 ? 2 : 4)) + 512 + 15) & ~size_t(15);
 }
 
-__device__ __forceinline__ BlockedBuf carve_blockedbuf(uint8_t* base, int cap) {
+__device__ __forceinline__ BlockedBuf carve_blockedbuf(uint8_t* base, int cap, bool pt16, bool meta) {
     BlockedBuf w;
     w.G = reinterpret_cast<uint64_t*>(base);
     w.it = reinterpret_cast<uint32_t*>(w.G + cap + 1);
@@ -58,8 +67,9 @@ __device__ __forceinline__ BlockedBuf carve_blockedbuf(uint8_t* base, int cap) {
     w.M = w.list + cap;
     w.qe = w.M + cap;
     w.qf = w.qe + 64;
-    w.NX = reinterpret_cast<uint16_t*>(w.qf + 64);
-    w.meta = w.NX + cap;
+    w.wd = w.qf + 64;
+    w.meta = reinterpret_cast<uint16_t*>(w.wd + (pt16 ? 0 : cap));
+    w.pt = w.meta + (meta ? cap : 0);
     return w;
 }
 
@@ -138,10 +148,12 @@ __device__ __forceinline__ uint32_t survivor_track(Survivors& s, uint32_t x) {
 
 // Moves the survivors (residual > 0, LCA depths as left by survivor_track)
 // of the lanes' blocks to a new blocked layout through the staging area (the
-// prefix array, free at this point), items with their meta, and returns the
+// prefix array, free at this point), items with their meta (and, PT16, their
+// point ids), and returns the
 // next depth to visit among the bits of `kmask` (-1: none).  On return Keff
 // and n describe the new layout and (ls, nh, nl) are the carries' inputs for
 // that depth.
+template <bool PT16, bool META>
 __device__ __forceinline__ int blocked_compact(const BlockedBuf& w, int& Keff, int& n, const Survivors& s,
                                                uint32_t kmask, uint64_t& ls, int& nh, uint64_t& nl) {
     const unsigned lane = lane_id();
@@ -171,7 +183,10 @@ __device__ __forceinline__ int blocked_compact(const BlockedBuf& w, int& Keff, i
             uint32_t x = w.it[base + t];
             if (it_res(x) > 0) {
                 if (j == off) x = (x & ~(31u << 25)) | (first_dp1 << 25);
-                w.G[j] = uint64_t(x) | (uint64_t(w.meta[base + t]) << 32);
+                uint64_t e = uint64_t(x);
+                if (META) e |= uint64_t(w.meta[base + t]) << 32;
+                if (PT16) e |= uint64_t(w.pt[base + t]) << 48;
+                w.G[j] = e;
                 ++j;
             }
         }
@@ -190,7 +205,8 @@ __device__ __forceinline__ int blocked_compact(const BlockedBuf& w, int& Keff, i
         const uint64_t e = pos < n_new ? w.G[pos] : 0ull;  // padding: no mass, a run head at every depth
         const uint32_t x = uint32_t(e);
         w.it[pos] = x;
-        w.meta[pos] = uint16_t(e >> 32);
+        if (META) w.meta[pos] = uint16_t(e >> 32);
+        if (PT16) w.pt[pos] = uint16_t(e >> 48);
         if (int(it_dp1(x)) <= knext) {
             nh = pos;
             nl = ls;
@@ -201,12 +217,52 @@ __device__ __forceinline__ int blocked_compact(const BlockedBuf& w, int& Keff, i
     return knext;
 }
 
+
+// Prices the first cnt (<= 32) queued pairs: acc += f * ||x_a - y_b||, and
+// with SAVE the distance goes to the pair's flow slot (queue entry j was
+// saved in slot qslot + j).  The queue holds the pairs' ground-point ids
+// (PT16) or their support indices, resolved through the staged ids.  MODE as
+// in price_queue.
+template <int MODE, bool SAVE, bool PT16>
+__device__ __forceinline__ void price_staged(const FlowCtx& c, const BlockedBuf& w, const Tables& tb, int na, int cnt,
+                                             int64_t qslot, CompSum& acc) {
+    const unsigned lane = lane_id();
+    uint32_t my_wa = 0, my_wb = 0;
+    if (int(lane) < cnt) {
+        const uint32_t q = w.qe[lane];
+        my_wa = PT16 ? (q & 0xFFFFu) : w.wd[q & 0xFFFFu];
+        my_wb = PT16 ? (q >> 16) : w.wd[na + (q >> 16)];
+    }
+    if (MODE == 0) {
+        if (int(lane) < cnt) {
+            const float dist = dist_lane(tb, c.dim, my_wa, my_wb);
+            acc.add(float(w.qf[lane]) * dist);
+            if (SAVE) c.f_dist[qslot + lane] = dist;
+        }
+    } else {
+        const unsigned grp = lane >> 3, sub = lane & 7u;
+        for (int r0 = 0; r0 < cnt; r0 += 4) {
+            const int e = r0 + int(grp);
+            uint32_t wa = __shfl_sync(FULL_MASK, my_wa, e & 31);
+            uint32_t wb = __shfl_sync(FULL_MASK, my_wb, e & 31);
+            if (e >= cnt) wa = wb = 0;  // idle group: a zero-length pair (row 0 twice)
+            // every lane takes part: dist_group shuffles across the warp
+            const float dist = dist_group<MODE>(c, wa, wb, sub);
+            if (e < cnt && sub == 0) {
+                acc.add(float(w.qf[e]) * dist);
+                if (SAVE) c.f_dist[qslot + e] = dist;
+            }
+        }
+    }
+}
+
 // Computes one pair with the warp, n = na + nb <= cap (the buffer's
 // capacity, a multiple of 32 with cap / 32 odd); returns the Flowtree value
 // on all lanes.
-template <int MODE, bool SAVE>
+template <int MODE, bool SAVE, bool PT16>
 __device__ float flowtree_pair_blocked(const FlowCtx& c, const BlockedBuf& w, const Tables& tb, int64_t pair,
                                        int64_t da, int64_t db) {
+    constexpr bool META = SAVE || !PT16;  // blocked_has_meta
     const unsigned lane = lane_id();
     const unsigned lmask_lt = lanemask_lt();
     const int64_t ao = c.a_ptr[da], bo = c.b_ptr[db];
@@ -217,28 +273,35 @@ __device__ float flowtree_pair_blocked(const FlowCtx& c, const BlockedBuf& w, co
     int Keff = blocked_k(n);
 
     // 1. stage ranks (words [0, n)) and masses (words [n, 2n)) of both
-    //    supports in the prefix array's space, eight loads in flight per lane
+    //    supports in the prefix array's space, and their ground-point ids
+    //    (PT16: in the list's space until the merge moves them to their
+    //    positions; else for the whole pair), 24 loads in flight per lane
     uint32_t* s32 = reinterpret_cast<uint32_t*>(w.G);
-    for (int b0 = 0; b0 < max(na, nb); b0 += 64) {
-        uint32_t v[8];
+    uint32_t* swd = PT16 ? w.list : w.wd;
+    for (int b0 = 0; b0 < max(na, nb); b0 += 128) {
+        uint32_t v[24];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < 4; ++u) {
             const int i = b0 + 32 * u + int(lane);
             v[u] = i < na ? __ldg(c.a_rank + ao + i) : 0u;
-            v[2 + u] = i < na ? __ldg(c.a_mass + ao + i) : 0u;
-            v[4 + u] = i < nb ? __ldg(c.b_rank + bo + i) : 0u;
-            v[6 + u] = i < nb ? __ldg(c.b_mass + bo + i) : 0u;
+            v[4 + u] = i < na ? __ldg(c.a_mass + ao + i) : 0u;
+            v[8 + u] = i < na ? __ldg(c.a_word + ao + i) : 0u;
+            v[12 + u] = i < nb ? __ldg(c.b_rank + bo + i) : 0u;
+            v[16 + u] = i < nb ? __ldg(c.b_mass + bo + i) : 0u;
+            v[20 + u] = i < nb ? __ldg(c.b_word + bo + i) : 0u;
         }
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < 4; ++u) {
             const int i = b0 + 32 * u + int(lane);
             if (i < na) {
                 s32[i] = v[u];
-                s32[n + i] = v[2 + u];
+                s32[n + i] = v[4 + u];
+                swd[i] = v[8 + u];
             }
             if (i < nb) {
-                s32[na + i] = v[4 + u];
-                s32[n + na + i] = v[6 + u];
+                s32[na + i] = v[12 + u];
+                s32[n + na + i] = v[16 + u];
+                swd[na + i] = v[20 + u];
             }
         }
     }
@@ -248,8 +311,6 @@ __device__ float flowtree_pair_blocked(const FlowCtx& c, const BlockedBuf& w, co
     //    [l*Keff, (l+1)*Keff)); the LCA depth to the previous item (from the
     //    range-minimum table); a point carried by both supports (equal ranks,
     //    mu first) is matched with itself here (the point level, distance 0).
-    //    Point-level pairs are parked in list/M (as ia | ib << 16, f) until
-    //    their flow slots are known.
     uint32_t levelmask = 0;
     int n_pt = 0;
     uint32_t first_rank = 0xFFFFFFFFu, last_rank = 0xFFFFFFFFu, last_res = 0, first_res = 0;
@@ -268,18 +329,20 @@ __device__ float flowtree_pair_blocked(const FlowCtx& c, const BlockedBuf& w, co
         uint32_t bj = j < nb ? B[j] : 0xFFFFFFFFu;
         for (int t = 0; t < Keff; ++t) {
             const int pos = base0 + t;
-            uint32_t rk = 0xFFFFFFFFu, r = 0, mi = 0;  // padding: no mass, a run head at every depth
+            uint32_t rk = 0xFFFFFFFFu, r = 0, mi = 0, pid = 0;  // padding: no mass, a run head at every depth
             if (pos < n) {
                 if (ai <= bj) {
                     rk = ai;
                     r = s32[n + i];
                     mi = uint32_t(i);
+                    if (PT16) pid = swd[i];
                     ++i;
                     ai = i < na ? A[i] : 0xFFFFFFFFu;
                 } else {
                     rk = bj;
                     r = s32[n + na + j];
                     mi = 0x8000u | uint32_t(j);
+                    if (PT16) pid = swd[na + j];
                     ++j;
                     bj = j < nb ? B[j] : 0xFFFFFFFFu;
                 }
@@ -291,10 +354,6 @@ __device__ float flowtree_pair_blocked(const FlowCtx& c, const BlockedBuf& w, co
                     const uint32_t f = min(last_res, r);
                     r -= f;
                     w.it[pos - 1] -= f;
-                    if (SAVE) {
-                        w.list[base0 + n_pt] = (uint32_t(w.meta[pos - 1]) & 0x7FFFu) | ((mi & 0x7FFFu) << 16);
-                        w.M[base0 + n_pt] = f;
-                    }
                     ++n_pt;
                 } else {
                     const int dd = lca_ranks(tb, c.n_points, last_rank, rk);
@@ -303,7 +362,8 @@ __device__ float flowtree_pair_blocked(const FlowCtx& c, const BlockedBuf& w, co
                 }
             }
             w.it[pos] = it_make(r, dp1, mi >> 15);
-            w.meta[pos] = uint16_t(mi);
+            if (META) w.meta[pos] = uint16_t(mi);
+            if (PT16) w.pt[pos] = uint16_t(pid);
             if (t == 0) {
                 first_rank = rk;
                 first_res = r;
@@ -324,12 +384,6 @@ __device__ float flowtree_pair_blocked(const FlowCtx& c, const BlockedBuf& w, co
             if (first_rank == prev_rank) {
                 const uint32_t f = min(prev_res, first_res);
                 x = it_make(it_res(x) - f, uint32_t(L + 2), it_side(x));
-                if (SAVE) {
-                    // the previous lane's last item is the mu item of this point
-                    w.list[base0 + n_pt] = (uint32_t(w.meta[base0 - 1]) & 0x7FFFu) |
-                                           ((uint32_t(w.meta[base0]) & 0x7FFFu) << 16);
-                    w.M[base0 + n_pt] = f;
-                }
                 ++n_pt;
             } else {
                 const int dd = lca_ranks(tb, c.n_points, prev_rank, first_rank);
@@ -348,17 +402,23 @@ __device__ float flowtree_pair_blocked(const FlowCtx& c, const BlockedBuf& w, co
     int n_saved = 0;
     const int64_t slot0 = SAVE ? c.slot_ptr[pair] : 0;
     if (SAVE) {
+        // point-level pairs: the nu item of each (LCA depth L + 1 to the mu
+        // item before it) writes the record; the flow is the smaller of the
+        // two staged masses
         __syncwarp();
         const uint32_t incl = warp_incl_scan_u32(uint32_t(n_pt));
-        const int o = int(incl) - n_pt;
-        for (int q = 0; q < n_pt; ++q) {
-            const uint32_t e = w.list[base0 + q];
-            const int64_t slot = slot0 + o + q;
-            c.f_ia[slot] = e & 0xFFFFu;
-            c.f_ib[slot] = e >> 16;
-            c.f_f[slot] = w.M[base0 + q];
-            c.f_depth[slot] = uint8_t(L + 1);
-            c.f_dist[slot] = 0.0f;
+        int64_t slot = slot0 + int(incl) - n_pt;
+        for (int t = 0; t < Keff; ++t) {
+            const int pos = base0 + t;
+            if (pos < n && it_dp1(w.it[pos]) == uint32_t(L + 2)) {
+                const uint32_t ia = uint32_t(w.meta[pos - 1]) & 0x7FFFu, ib = uint32_t(w.meta[pos]) & 0x7FFFu;
+                c.f_ia[slot] = ia;
+                c.f_ib[slot] = ib;
+                c.f_f[slot] = min(s32[n + ia], s32[n + na + ib]);
+                c.f_depth[slot] = uint8_t(L + 1);
+                c.f_dist[slot] = 0.0f;
+                ++slot;
+            }
         }
         n_saved = int(__shfl_sync(FULL_MASK, incl, 31));
     }
@@ -374,14 +434,11 @@ __device__ float flowtree_pair_blocked(const FlowCtx& c, const BlockedBuf& w, co
             const uint32_t y = survivor_track(sv, x);
             if (y != x) w.it[base0 + t] = y;
         }
-        k = blocked_compact(w, Keff, n, sv, levelmask & ((2u << L) - 1u), ls, nh, nl);
+        k = blocked_compact<PT16, META>(w, Keff, n, sv, levelmask & ((2u << L) - 1u), ls, nh, nl);
     }
 
     int qn = 0;                                  // pairs queued for pricing
     int64_t qslot = SAVE ? slot0 + n_saved : 0;  // flow slot of queue entry 0
-    WarpBuf qb{};
-    qb.qe = w.qe;
-    qb.qf = w.qf;
     const uint32_t* G32 = reinterpret_cast<const uint32_t*>(w.G);  // G32[2p] = mu prefix, G32[2p + 1] = nu prefix
 
     // 4. bottom-up matching over the depths where the sides meet, deepest first
@@ -390,8 +447,8 @@ __device__ float flowtree_pair_blocked(const FlowCtx& c, const BlockedBuf& w, co
         uint64_t g0, S_in;
         int h_in;
         blocked_carries(ls, nh, nl, &g0, &h_in, &S_in);
-        // walk 1: prefixes of every position; at run heads the link to the
-        // next head and the run's matched mass M = min(mu total, nu total)
+        // walk 1: prefixes of every position; at run heads the run's matched
+        // mass M = min(mu total, nu total)
         {
             uint32_t glo = uint32_t(g0), ghi = uint32_t(g0 >> 32);
             uint32_t slo = uint32_t(S_in), shi = uint32_t(S_in >> 32);
@@ -402,7 +459,6 @@ __device__ float flowtree_pair_blocked(const FlowCtx& c, const BlockedBuf& w, co
                 if (int(it_dp1(x)) <= k) {
                     if (cur >= 0) {
                         w.M[cur] = min(glo - slo, ghi - shi);
-                        w.NX[cur] = uint16_t(pos);
                     }
                     slo = glo;
                     shi = ghi;
@@ -414,7 +470,6 @@ __device__ float flowtree_pair_blocked(const FlowCtx& c, const BlockedBuf& w, co
             if (lane == 31) {
                 const int end = 32 * Keff;
                 w.M[cur] = min(glo - slo, ghi - shi);
-                w.NX[cur] = uint16_t(end);
                 w.G[end] = uint64_t(glo) | (uint64_t(ghi) << 32);
             }
         }
@@ -444,7 +499,7 @@ __device__ float flowtree_pair_blocked(const FlowCtx& c, const BlockedBuf& w, co
                 const unsigned em = __ballot_sync(FULL_MASK, emit);
                 uint32_t y = x;
                 if (emit) {
-                    w.list[total + __popc(em & lmask_lt)] = uint32_t(pos) | hp;
+                    w.list[total + __popc(em & lmask_lt)] = uint32_t(pos) | (side << 15) | hp;
                     y = x - min(r, M - P);
                 }
                 total += __popc(em);
@@ -458,13 +513,12 @@ __device__ float flowtree_pair_blocked(const FlowCtx& c, const BlockedBuf& w, co
             const int e = e0 + int(lane);
             bool emit = false;
             uint32_t f = 0;
-            unsigned ia = 0, ib = 0;
+            unsigned ia = 0, ib = 0, qa = 0, qb = 0;
             if (e < total) {
                 const uint32_t ent = w.list[e];
-                const int pos = int(ent & 0xFFFFu), h = int(ent >> 16);
-                const unsigned mi = w.meta[pos];
-                const unsigned own = mi >> 15, oth = own ^ 1u;
-                const int nx = int(w.NX[h]);
+                const int pos = int(ent & 0x7FFFu), h = int(ent >> 16);
+                const unsigned own = (ent >> 15) & 1u, oth = own ^ 1u;
+                const int nx = 32 * Keff;  // the layout's end
                 const uint32_t M = w.M[h];
                 const uint32_t S_own = G32[2 * h + own], S_oth = G32[2 * h + oth];
                 const uint32_t g_own = G32[2 * pos + own];
@@ -472,8 +526,9 @@ __device__ float flowtree_pair_blocked(const FlowCtx& c, const BlockedBuf& w, co
                 const uint32_t P = g_own - S_own;
                 const uint32_t t0 = S_oth + P;
                 const uint32_t capv = S_oth + min(P + r, M);
-                // the other-side item holding offset P: last position in
-                // the run whose other-side prefix is <= t0
+                // the other-side item holding offset P: last position whose
+                // other-side prefix is <= t0 (it lies in the run: the prefix
+                // at the run's end exceeds t0)
                 int lo = h, hi = nx;
                 while (hi - lo > 1) {
                     const int mid = (lo + hi) >> 1;
@@ -483,13 +538,15 @@ __device__ float flowtree_pair_blocked(const FlowCtx& c, const BlockedBuf& w, co
                 if (!(own == 1u && gp == t0)) {
                     f = min(capv, G32[2 * lo + 2 + oth]) - t0;
                     emit = true;
-                    const unsigned mp = w.meta[lo];
-                    if (own == 0u) {
-                        ia = mi & 0x7FFFu;
-                        ib = mp & 0x7FFFu;
-                    } else {
-                        ia = mp & 0x7FFFu;
-                        ib = mi & 0x7FFFu;
+                    if (META) {
+                        const unsigned mi = w.meta[pos], mp = w.meta[lo];
+                        ia = (own ? mp : mi) & 0x7FFFu;
+                        ib = (own ? mi : mp) & 0x7FFFu;
+                    }
+                    if (PT16) {
+                        const uint32_t po = w.pt[pos], pp = w.pt[lo];
+                        qa = own ? pp : po;
+                        qb = own ? po : pp;
                     }
                 }
             }
@@ -497,7 +554,7 @@ __device__ float flowtree_pair_blocked(const FlowCtx& c, const BlockedBuf& w, co
             if (emask == 0) continue;
             const int qp = __popc(emask & lmask_lt);
             if (emit) {
-                w.qe[qn + qp] = ia | (ib << 16);
+                w.qe[qn + qp] = PT16 ? (qa | (qb << 16)) : (ia | (ib << 16));
                 w.qf[qn + qp] = f;
             }
             if (SAVE) {
@@ -513,7 +570,7 @@ __device__ float flowtree_pair_blocked(const FlowCtx& c, const BlockedBuf& w, co
             qn += __popc(emask);
             if (qn >= 32) {
                 __syncwarp();
-                price_queue<MODE, SAVE>(c, qb, tb, ao, bo, 32, qslot, acc);
+                price_staged<MODE, SAVE, PT16>(c, w, tb, na, 32, qslot, acc);
                 __syncwarp();
                 const int rest = qn - 32;
                 uint32_t qe2 = 0, qf2 = 0;
@@ -532,11 +589,11 @@ __device__ float flowtree_pair_blocked(const FlowCtx& c, const BlockedBuf& w, co
             }
         }
         __syncwarp();  // the list walk above read the prefix array the compaction reuses
-        k = blocked_compact(w, Keff, n, sv, (1u << k) - 1u, ls, nh, nl);
+        k = blocked_compact<PT16, META>(w, Keff, n, sv, (1u << k) - 1u, ls, nh, nl);
     }
     if (qn > 0) {
         __syncwarp();
-        price_queue<MODE, SAVE>(c, qb, tb, ao, bo, qn, qslot, acc);
+        price_staged<MODE, SAVE, PT16>(c, w, tb, na, qn, qslot, acc);
     }
     {  // any mass left unmatched would be a bug: report it
         bool left = false;

@@ -40,6 +40,10 @@ def cases():
     v30 = synth.mixture_vocab(3000, 30, 50, 0.3, 8)
     out["d30"] = (v30, 12, synth.random_shift(30, 9), synth.zipf_docs(3000, 120, 10, median=40, s_lo=5, s_hi=200),
                   synth.zipf_docs(3000, 4, 11, median=40, s_lo=5, s_hi=200))
+    # more than 65,536 ground points: the blocked form's per-support point ids
+    wide = np.random.default_rng(16).random((70000, 2)).astype(np.float32)
+    out["wide2d"] = (wide, 12, synth.random_shift(2, 17), synth.uniform_docs(70000, 120, 10, 60, 18),
+                     synth.uniform_docs(70000, 4, 10, 60, 19))
     v300 = synth.mixture_vocab(4000, 300, 100, 0.3, 12)
     out["d300"] = (v300, 12, synth.random_shift(300, 13),
                    synth.zipf_docs(4000, 100, 14, median=80, s_lo=20, s_hi=400),
@@ -80,12 +84,13 @@ def _oracle_costs(otree, pts, SA, SB, pa, pb):
 
 
 def algo_cases(names):
-    """(case, algorithm): every case with the default, plus both algorithms where dim <= 8."""
+    """(case, algorithm): every case with the default (the blocked form where the pairs fit it) and the
+    compacting warp form, plus the thread form where dim <= 8."""
     out = []
     for n in names:
-        out.append((n, 0))
+        out += [(n, 0), (n, 1)]
         if CASES[n][0].shape[1] <= 8:
-            out += [(n, 1), (n, 2)]
+            out.append((n, 2))
     return out
 
 
@@ -115,7 +120,7 @@ def test_flowtree_cross_and_pairs_vs_oracle(name, algo):
     assert tree.status() == 0
 
 
-@pytest.mark.parametrize("name,algo", algo_cases(["tiny2d", "d300", "line", "grid"]))
+@pytest.mark.parametrize("name,algo", algo_cases(["tiny2d", "d300", "line", "grid", "wide2d"]))
 def test_saved_flows_bit_exact(name, algo):
     pts, L, shift, db, _ = CASES[name]
     tree, otree = build_both(pts, L, shift)
