@@ -423,26 +423,27 @@ __device__ float flowtree_pair_blocked(const FlowCtx& c, const BlockedBuf& w, co
         n_saved = int(__shfl_sync(FULL_MASK, incl, 31));
     }
     __syncwarp();
-    // 3. the survivors of the point level, and the first depth to visit
-    uint64_t ls, nl;
-    int nh;
-    int k;
-    {
-        Survivors sv;
-        for (int t = 0; t < Keff; ++t) {
-            const uint32_t x = w.it[base0 + t];
-            const uint32_t y = survivor_track(sv, x);
-            if (y != x) w.it[base0 + t] = y;
-        }
-        k = blocked_compact<PT16, META>(w, Keff, n, sv, levelmask & ((2u << L) - 1u), ls, nh, nl);
+    // 3. the survivors of the point level
+    Survivors sv;
+    for (int t = 0; t < Keff; ++t) {
+        const uint32_t x = w.it[base0 + t];
+        const uint32_t y = survivor_track(sv, x);
+        if (y != x) w.it[base0 + t] = y;
     }
+    uint32_t kmask = levelmask & ((2u << L) - 1u);
 
     int qn = 0;                                  // pairs queued for pricing
     int64_t qslot = SAVE ? slot0 + n_saved : 0;  // flow slot of queue entry 0
     const uint32_t* G32 = reinterpret_cast<const uint32_t*>(w.G);  // G32[2p] = mu prefix, G32[2p + 1] = nu prefix
 
-    // 4. bottom-up matching over the depths where the sides meet, deepest first
-    while (k >= 0) {
+    // 4. bottom-up matching over the depths where the sides meet, deepest
+    //    first: every pass starts with the compaction of the survivors (one
+    //    call site keeps the kernel small), which also names the next depth
+    for (;;) {
+        uint64_t ls, nl;
+        int nh;
+        const int k = blocked_compact<PT16, META>(w, Keff, n, sv, kmask, ls, nh, nl);
+        if (k < 0) break;
         const int base = int(lane) * Keff;
         uint64_t g0, S_in;
         int h_in;
@@ -477,7 +478,7 @@ __device__ float flowtree_pair_blocked(const FlowCtx& c, const BlockedBuf& w, co
         // walk 2: residual updates, the list of matching items (by ballot),
         // and the survivor bookkeeping of the compaction
         int total = 0;
-        Survivors sv;
+        sv = Survivors();
         {
             uint32_t rlo = uint32_t(g0) - uint32_t(S_in), rhi = uint32_t(g0 >> 32) - uint32_t(S_in >> 32);
             uint32_t M = h_in >= 0 ? w.M[h_in] : 0u;
@@ -589,7 +590,7 @@ __device__ float flowtree_pair_blocked(const FlowCtx& c, const BlockedBuf& w, co
             }
         }
         __syncwarp();  // the list walk above read the prefix array the compaction reuses
-        k = blocked_compact<PT16, META>(w, Keff, n, sv, (1u << k) - 1u, ls, nh, nl);
+        kmask = (1u << k) - 1u;
     }
     if (qn > 0) {
         __syncwarp();
