@@ -275,33 +275,33 @@ __device__ float flowtree_pair_blocked(const FlowCtx& c, const BlockedBuf& w, co
     // 1. stage ranks (words [0, n)) and masses (words [n, 2n)) of both
     //    supports in the prefix array's space, and their ground-point ids
     //    (PT16: in the list's space until the merge moves them to their
-    //    positions; else for the whole pair), 24 loads in flight per lane
+    //    positions; else for the whole pair), 12 loads in flight per lane
     uint32_t* s32 = reinterpret_cast<uint32_t*>(w.G);
     uint32_t* swd = PT16 ? w.list : w.wd;
-    for (int b0 = 0; b0 < max(na, nb); b0 += 128) {
-        uint32_t v[24];
+    for (int b0 = 0; b0 < max(na, nb); b0 += 64) {
+        uint32_t v[12];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < 2; ++u) {
             const int i = b0 + 32 * u + int(lane);
             v[u] = i < na ? __ldg(c.a_rank + ao + i) : 0u;
-            v[4 + u] = i < na ? __ldg(c.a_mass + ao + i) : 0u;
-            v[8 + u] = i < na ? __ldg(c.a_word + ao + i) : 0u;
-            v[12 + u] = i < nb ? __ldg(c.b_rank + bo + i) : 0u;
-            v[16 + u] = i < nb ? __ldg(c.b_mass + bo + i) : 0u;
-            v[20 + u] = i < nb ? __ldg(c.b_word + bo + i) : 0u;
+            v[2 + u] = i < na ? __ldg(c.a_mass + ao + i) : 0u;
+            v[4 + u] = i < na ? __ldg(c.a_word + ao + i) : 0u;
+            v[6 + u] = i < nb ? __ldg(c.b_rank + bo + i) : 0u;
+            v[8 + u] = i < nb ? __ldg(c.b_mass + bo + i) : 0u;
+            v[10 + u] = i < nb ? __ldg(c.b_word + bo + i) : 0u;
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < 2; ++u) {
             const int i = b0 + 32 * u + int(lane);
             if (i < na) {
                 s32[i] = v[u];
-                s32[n + i] = v[4 + u];
-                swd[i] = v[8 + u];
+                s32[n + i] = v[2 + u];
+                swd[i] = v[4 + u];
             }
             if (i < nb) {
-                s32[na + i] = v[12 + u];
-                s32[n + na + i] = v[16 + u];
-                swd[na + i] = v[20 + u];
+                s32[na + i] = v[6 + u];
+                s32[n + na + i] = v[8 + u];
+                swd[na + i] = v[10 + u];
             }
         }
     }
