@@ -544,16 +544,30 @@ def extras(args, tree, D, Q, q_h, db_h, pts, shift, batched_value, dev, pk, pk_k
         api.flowtree_batch(t2, t2.points, A, B, flows.pair_a, flows.pair_b, flows=flows, out=cst, workspace=fws)
         api.flowtree_backward(t2, A, B, flows, t2.points, gcost, grad_vocab=gv, workspace=bws)
 
-    for _ in range(3):
-        fb()
-    torch.cuda.synchronize()
-    e0.record()
+    # the step a user writes: loss = sum of Flowtree values through torch.autograd, the adjoint into the
+    # vocabulary's gradient; the flows are held by the caller (created once for these pairs)
+    vparam = t2.points.clone().requires_grad_(True)
+
+    def fb_autograd(fl):
+        vparam.grad = None
+        api.flowtree(vparam, t2, A, B, idx, idx, flows=fl).sum().backward()
+
+    def timed(fn, reps=10):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
     reps = 10
-    for _ in range(reps):
-        fb()
-    e1.record()
-    e1.synchronize()
-    fb_ms = e0.elapsed_time(e1) / reps
+    fb_ms = timed(lambda: fb_autograd(flows), reps)
+    rebind = api.Flows.with_capacity(t2, A, B, npairs)
+    fb_rebind_ms = timed(lambda: fb_autograd(rebind))
+    raw_ms = timed(fb)
     e0.record()
     for _ in range(reps):
         api.flowtree_batch(t2, t2.points, A, B, flows.pair_a, flows.pair_b, out=cst, workspace=fws)
@@ -568,6 +582,10 @@ def extras(args, tree, D, Q, q_h, db_h, pts, shift, batched_value, dev, pk, pk_k
     b_ms = e0.elapsed_time(e1) / reps
     out["fwd_bwd"] = {"value": npairs / (fb_ms * 1e-3), "unit": UNIT, "forward_only": npairs / (f_ms * 1e-3),
                       "ms_per_step": fb_ms, "backward_ms": b_ms,
+                      "path": "torch.autograd: api.flowtree(vocab, ...).sum().backward(), caller-held flows",
+                      "raw_api_ms_per_step": raw_ms,
+                      "rebinding_flows": {"value": npairs / (fb_rebind_ms * 1e-3), "ms_per_step": fb_rebind_ms,
+                                          "note": "Flows.with_capacity rebound every step (pairs may change)"},
                       "workload": "vocab %d x 300 (1,000-cluster mixture), %d doc pairs, lengths 20-300" % (nw, npairs)}
 
     # text-shaped kNN pipeline

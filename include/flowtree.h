@@ -273,6 +273,24 @@ ft_status ft_flows_capacity(const ft_flows* f, int64_t* n_pairs, int64_t* capaci
 ft_status ft_flows_export(const ft_flows* f, int64_t* slot_ptr_host, int32_t* count_host, uint32_t* item_a_host,
                           uint32_t* item_b_host, uint32_t* flow_host, uint8_t* depth_host);
 
+/* Rebindable saved flows, for a training loop whose pairs change every step:
+ * ft_flows_create_capacity allocates (once, without synchronising) room for
+ * any max_pairs pairs of the document sets a and b, i.e. max_pairs *
+ * (a's longest support + b's longest support) slots; ft_flows_bind then
+ * points the flows at a pair list (pair_a_dev/pair_b_dev, n_pairs <=
+ * max_pairs, copied on `stream`; both NULL = the a x b cross product, which
+ * must then have at most max_pairs pairs) with no allocation and no host
+ * synchronisation: the slot offsets are computed on the device.  The bound
+ * flows go to ft_flowtree_batch (with the same pairs) and to
+ * ft_flowtree_backward exactly like those of ft_flows_create; the adjoint's
+ * work grows with the capacity, not only with the bound pairs.  a and b
+ * must outlive the flows.  Pair indices out of range flag FT_EINVAL in the
+ * tree's status word (ft_tree_status). */
+ft_status ft_flows_create_capacity(const ft_tree* t, const ft_docs* a, const ft_docs* b, int64_t max_pairs,
+                                   ft_flows** out);
+ft_status ft_flows_bind(ft_flows* f, const int32_t* pair_a_dev, const int32_t* pair_b_dev, int64_t n_pairs,
+                        void* stream);
+
 /* ------------------------------------------------------------------------
  * Adjoint of the Flowtree estimate for the frozen flow (derived from the
  * pricing sum of Sec. 3; the paper does not differentiate):

@@ -67,6 +67,8 @@ SIGNATURES = {
     "ft_flows_free": (None, [vp]),
     "ft_flows_capacity": (i32, [vp, C.POINTER(i64), C.POINTER(i64)]),
     "ft_flows_export": (i32, [vp, vp, vp, vp, vp, vp, vp]),
+    "ft_flows_create_capacity": (i32, [vp, vp, vp, i64, C.POINTER(vp)]),
+    "ft_flows_bind": (i32, [vp, vp, vp, i64, vp]),
     "ft_flowtree_backward_workspace_size": (sz, [vp, vp]),
     "ft_flowtree_backward": (i32, [vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]),
     "ft_quadtree_scan_workspace_size": (sz, [vp, vp, vp, i32]),

@@ -185,7 +185,8 @@ class Docs:
 
 
 class Flows:
-    """Saved tree flows of a batch of pairs (ft_flows_create)."""
+    """Saved tree flows of a batch of pairs (ft_flows_create), or rebindable
+    flows sized for up to max_pairs pairs (Flows.with_capacity + bind)."""
 
     def __init__(self, tree: Tree, a: Docs, b: Docs, pair_a=None, pair_b=None, stream=None):
         lib = _ffi.load()
@@ -197,6 +198,28 @@ class Flows:
         check(code, "ft_flows_create")
         self._h = h
         self.n_pairs = n_pairs
+        self.max_pairs = 0
+
+    @classmethod
+    def with_capacity(cls, tree: Tree, a: Docs, b: Docs, max_pairs: int) -> "Flows":
+        """Flows with room for any max_pairs pairs of (a, b), allocated once (ft_flows_create_capacity)."""
+        self = cls.__new__(cls)
+        self.tree, self.a, self.b = tree, a, b
+        h = C.c_void_p()
+        check(_ffi.load().ft_flows_create_capacity(tree.handle, a.handle, b.handle, int(max_pairs), C.byref(h)),
+              "ft_flows_create_capacity")
+        self._h = h
+        self.max_pairs = int(max_pairs)
+        self.pair_a = self.pair_b = None
+        self.n_pairs = 0
+        return self
+
+    def bind(self, pair_a=None, pair_b=None, stream=None) -> "Flows":
+        """Point the flows at a pair list (None, None = the cross product): no allocation, no host sync."""
+        pa, pb, n_pairs = _pairs(self.a, self.b, pair_a, pair_b, self.tree.device)
+        check(_ffi.load().ft_flows_bind(self._h, _ptr(pa), _ptr(pb), n_pairs, _stream(stream)), "ft_flows_bind")
+        self.pair_a, self.pair_b, self.n_pairs = pa, pb, n_pairs
+        return self
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -454,8 +477,12 @@ class FlowtreeFunction(torch.autograd.Function):
     """
 
     @staticmethod
-    def forward(ctx, vocab, tree, a, b, pair_a, pair_b):
-        flows = Flows(tree, a, b, pair_a, pair_b)
+    def forward(ctx, vocab, tree, a, b, pair_a, pair_b, flows=None):
+        if flows is None:
+            flows = Flows(tree, a, b, pair_a, pair_b)
+        elif flows.max_pairs:  # caller-held rebindable flows: bound to this call's pairs (no allocation, no sync)
+            flows.bind(pair_a, pair_b)
+        # else: caller-held flows created for exactly these pairs, reused as they are
         cost = flowtree_batch(tree, vocab.detach(), a, b, flows.pair_a, flows.pair_b, flows=flows)
         ctx.tree, ctx.a, ctx.b, ctx.flows = tree, a, b, flows
         ctx.save_for_backward(vocab)
@@ -466,8 +493,12 @@ class FlowtreeFunction(torch.autograd.Function):
         (vocab,) = ctx.saved_tensors
         g = flowtree_backward(ctx.tree, ctx.a, ctx.b, ctx.flows, vocab.detach().contiguous(),
                               grad_cost.contiguous())
-        return g, None, None, None, None, None
+        return g, None, None, None, None, None, None
 
 
-def flowtree(vocab: torch.Tensor, tree: Tree, a: Docs, b: Docs, pair_a=None, pair_b=None) -> torch.Tensor:
-    return FlowtreeFunction.apply(vocab, tree, a, b, pair_a, pair_b)
+def flowtree(vocab: torch.Tensor, tree: Tree, a: Docs, b: Docs, pair_a=None, pair_b=None,
+             flows: Optional[Flows] = None) -> torch.Tensor:
+    """Differentiable Flowtree values (FlowtreeFunction).  flows: optional caller-held Flows reused across
+    calls, so a training step allocates and synchronises nothing: either created for exactly these pairs
+    (used as they are) or rebindable (Flows.with_capacity; bound to the pairs of each call)."""
+    return FlowtreeFunction.apply(vocab, tree, a, b, pair_a, pair_b, flows)

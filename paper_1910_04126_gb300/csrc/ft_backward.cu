@@ -70,9 +70,19 @@ __global__ void k_bwd_slots(const int64_t* __restrict__ slot_ptr, const int32_t*
                             const int64_t* __restrict__ b_ptr, const uint32_t* __restrict__ b_word,
                             const float* __restrict__ grad_cost, int levels, uint32_t sentinel,
                             uint32_t* __restrict__ key, uint32_t* __restrict__ s_wa, uint32_t* __restrict__ s_wb,
-                            float* __restrict__ s_coef) {
+                            float* __restrict__ s_coef, int64_t capacity) {
     const int64_t warps = int64_t(gridDim.x) * (blockDim.x / 32);
     const unsigned lane = lane_id();
+    // slots past the bound pairs' total (flows sized for more pairs than
+    // they hold) take no part: sentinel keys sort them last
+    for (int64_t s = slot_ptr[n_pairs] + int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < capacity;
+         s += int64_t(gridDim.x) * blockDim.x) {
+        key[2 * s] = sentinel;
+        key[2 * s + 1] = sentinel;
+        s_wa[s] = 0;
+        s_wb[s] = 0;
+        s_coef[s] = 0.0f;
+    }
     for (int64_t p = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) / 32; p < n_pairs; p += warps) {
         int64_t da, db;
         if (pair_a) {
@@ -438,8 +448,9 @@ extern "C" ft_status ft_flowtree_backward(const ft_tree* t, const ft_docs* a, co
 
     k_bwd_slots<<<grid_for(flows->n_pairs * 32, 256), 256, 0, s>>>(
         flows->d_slot_ptr, flows->d_count, flows->d_ia, flows->d_ib, flows->d_f, flows->d_depth, flows->d_dist,
-        flows->d_pair_a, flows->d_pair_b, flows->nb_cross, flows->n_pairs, a->d_ptr, a->d_word, b->d_ptr, b->d_word,
-        grad_cost_dev, t->levels, sentinel, l.key, l.s_wa, l.s_wb, l.s_coef);
+        flows->cross ? nullptr : flows->d_pair_a, flows->cross ? nullptr : flows->d_pair_b, flows->nb_cross,
+        flows->n_pairs, a->d_ptr, a->d_word, b->d_ptr, b->d_word, grad_cost_dev, t->levels, sentinel, l.key, l.s_wa,
+        l.s_wb, l.s_coef, flows->capacity);
     FT_TRY(ft_iota_u32(l.perm, ne, s));
     FT_TRY(ft_sort_perm_by_u32(l.key, l.perm, ne, key_bits, l.sort_tmp, s));
     FT_CUDA(cudaMemsetAsync(l.counters, 0, 2 * sizeof(uint32_t), s));

@@ -516,6 +516,7 @@ void free_flows(ft_flows* f) {
     cudaFree(f->d_f);
     cudaFree(f->d_depth);
     cudaFree(f->d_dist);
+    cudaFree(f->d_scan_tmp);
     delete f;
 }
 
@@ -723,5 +724,66 @@ extern "C" ft_status ft_flows_export(const ft_flows* f, int64_t* slot_ptr_host, 
     if (item_b_host) FT_CUDA(cudaMemcpy(item_b_host, f->d_ib, cap * 4, cudaMemcpyDeviceToHost));
     if (flow_host) FT_CUDA(cudaMemcpy(flow_host, f->d_f, cap * 4, cudaMemcpyDeviceToHost));
     if (depth_host) FT_CUDA(cudaMemcpy(depth_host, f->d_depth, cap, cudaMemcpyDeviceToHost));
+    return FT_OK;
+}
+
+extern "C" ft_status ft_flows_create_capacity(const ft_tree* t, const ft_docs* a, const ft_docs* b, int64_t max_pairs,
+                                              ft_flows** out) {
+    if (!out) return FT_EINVAL;
+    *out = nullptr;
+    if (!t || !a || !b || max_pairs < 1 || a->tree != t || b->tree != t) return FT_EINVAL;
+    const int64_t per_pair = int64_t(a->max_support) + b->max_support;
+    const int64_t cap = std::max<int64_t>(max_pairs * per_pair, 1);
+    ft_flows* f = new ft_flows;
+    f->tree = t;
+    f->a = a;
+    f->b = b;
+    f->max_pairs = max_pairs;
+    f->capacity = cap;
+    auto fail = [&](ft_status st) {
+        free_flows(f);
+        return st;
+    };
+    ft_status st;
+    if ((st = dmalloc(&f->d_pair_a, size_t(max_pairs))) != FT_OK) return fail(st);
+    if ((st = dmalloc(&f->d_pair_b, size_t(max_pairs))) != FT_OK) return fail(st);
+    if ((st = dmalloc(&f->d_slot_ptr, size_t(max_pairs) + 1)) != FT_OK) return fail(st);
+    if ((st = dmalloc(&f->d_count, size_t(max_pairs))) != FT_OK) return fail(st);
+    if ((st = dmalloc(&f->d_scan_tmp, ft_scan_tmp_elems(max_pairs + 1))) != FT_OK) return fail(st);
+    if ((st = dmalloc(&f->d_ia, size_t(cap))) != FT_OK) return fail(st);
+    if ((st = dmalloc(&f->d_ib, size_t(cap))) != FT_OK) return fail(st);
+    if ((st = dmalloc(&f->d_f, size_t(cap))) != FT_OK) return fail(st);
+    if ((st = dmalloc(&f->d_depth, size_t(cap))) != FT_OK) return fail(st);
+    if ((st = dmalloc(&f->d_dist, size_t(cap))) != FT_OK) return fail(st);
+    *out = f;
+    return FT_OK;
+}
+
+extern "C" ft_status ft_flows_bind(ft_flows* f, const int32_t* pair_a_dev, const int32_t* pair_b_dev, int64_t n_pairs,
+                                   void* stream) {
+    FtRange nvtx_range("ft_flows_bind");
+    if (!f || f->max_pairs == 0 || n_pairs < 0 || n_pairs > f->max_pairs) return FT_EINVAL;
+    if ((pair_a_dev == nullptr) != (pair_b_dev == nullptr)) return FT_EINVAL;
+    if (!pair_a_dev && n_pairs != f->a->n_docs * f->b->n_docs) return FT_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    f->cross = pair_a_dev == nullptr;
+    f->nb_cross = f->b->n_docs;
+    f->n_pairs = n_pairs;
+    if (n_pairs == 0) return FT_OK;
+    // the pair list is copied (the caller may reuse its buffers); a cross
+    // product keeps no list
+    const int32_t* pa = nullptr;
+    const int32_t* pb = nullptr;
+    if (pair_a_dev) {
+        FT_CUDA(cudaMemcpyAsync(f->d_pair_a, pair_a_dev, size_t(n_pairs) * 4, cudaMemcpyDeviceToDevice, s));
+        FT_CUDA(cudaMemcpyAsync(f->d_pair_b, pair_b_dev, size_t(n_pairs) * 4, cudaMemcpyDeviceToDevice, s));
+        pa = f->d_pair_a;
+        pb = f->d_pair_b;
+    }
+    k_slot_len<<<grid_for(n_pairs, 256), 256, 0, s>>>(f->a->d_ptr, f->b->d_ptr, pa, pb, n_pairs, f->b->n_docs,
+                                                      f->a->n_docs, f->b->n_docs, f->d_slot_ptr, f->tree->d_status);
+    FT_CUDA(cudaMemsetAsync(f->d_slot_ptr + n_pairs, 0, 8, s));
+    FT_TRY(ft_exclusive_scan_i64(f->d_slot_ptr, f->d_slot_ptr, n_pairs + 1, f->d_scan_tmp, s));
+    FT_CUDA(cudaMemsetAsync(f->d_count, 0, size_t(n_pairs) * 4, s));
     return FT_OK;
 }

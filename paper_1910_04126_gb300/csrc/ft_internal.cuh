@@ -103,6 +103,13 @@ struct ft_flows {
     uint32_t* d_f = nullptr;
     uint8_t* d_depth = nullptr;
     float* d_dist = nullptr;        // Euclidean distance of the pair (FP32)
+    // rebindable flows (ft_flows_create_capacity): capacity for any max_pairs
+    // pairs of these document sets, rebound to a pair list by ft_flows_bind
+    const ft_tree* tree = nullptr;
+    const ft_docs* a = nullptr;
+    const ft_docs* b = nullptr;
+    int64_t max_pairs = 0;          // 0: fixed pair list (ft_flows_create)
+    int64_t* d_scan_tmp = nullptr;  // [ft_scan_tmp_elems(max_pairs + 1)]
 };
 
 // ---------------------------------------------------------------------------

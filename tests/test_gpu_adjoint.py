@@ -186,3 +186,51 @@ def test_backward_single_point_runs_over_many_chunks():
     assert np.allclose(got[0], gs * u, rtol=1e-5, atol=1e-4)
     assert np.allclose(got[1], -gs * u, rtol=1e-5, atol=1e-4)
     assert np.all(got[2] == 0.0)
+
+
+def test_rebindable_flows_match_created_flows():
+    """Flows.with_capacity + bind (no allocation, no host sync per step) give the same values and bitwise the
+    same gradients as flows created for each pair list, over two binds in a row with different pair lists,
+    a cross-product bind, and through autograd."""
+    V, shift, A, B, tree, ot = setup(n_pairs=160, seed=7)
+    DA, DB = api.Docs.from_csr(tree, A), api.Docs.from_csr(tree, B)
+    rng = np.random.default_rng(8)
+    F = api.Flows.with_capacity(tree, DA, DB, 600)
+    for n in (600, 237):
+        pa = torch.as_tensor(rng.integers(0, A.n, n), dtype=torch.int32, device="cuda")
+        pb = torch.as_tensor(rng.integers(0, B.n, n), dtype=torch.int32, device="cuda")
+        gc = torch.as_tensor(rng.standard_normal(n).astype(np.float32), device="cuda")
+        F.bind(pa, pb)
+        c1 = api.flowtree_batch(tree, tree.points, DA, DB, pa, pb, flows=F)
+        g1 = api.flowtree_backward(tree, DA, DB, F, tree.points, gc)
+        ref = api.Flows(tree, DA, DB, pa, pb)
+        c2 = api.flowtree_batch(tree, tree.points, DA, DB, ref.pair_a, ref.pair_b, flows=ref)
+        g2 = api.flowtree_backward(tree, DA, DB, ref, tree.points, gc)
+        assert torch.equal(c1, c2)
+        assert torch.equal(g1, g2)
+        # the saved records themselves
+        got, want = F.export(), ref.export()
+        for i in range(n):
+            assert all(np.array_equal(x, y) for x, y in zip(got[i], want[i])), i
+    # a cross product bound to the same capacity
+    DAs, DBs = api.Docs.from_csr(tree, A.subset(np.arange(12))), api.Docs.from_csr(tree, B.subset(np.arange(40)))
+    Fx = api.Flows.with_capacity(tree, DAs, DBs, 12 * 40).bind()
+    gc = torch.ones(12 * 40, device="cuda")
+    c1 = api.flowtree_batch(tree, tree.points, DAs, DBs, flows=Fx)
+    g1 = api.flowtree_backward(tree, DAs, DBs, Fx, tree.points, gc)
+    ref = api.Flows(tree, DAs, DBs)
+    c2 = api.flowtree_batch(tree, tree.points, DAs, DBs, flows=ref)
+    g2 = api.flowtree_backward(tree, DAs, DBs, ref, tree.points, gc)
+    assert torch.equal(c1, c2) and torch.equal(g1, g2)
+    # autograd with the caller-held flows, two steps
+    vocab = tree.points.clone().requires_grad_(True)
+    for n in (300, 300):
+        pa = torch.as_tensor(rng.integers(0, A.n, n), dtype=torch.int32, device="cuda")
+        pb = torch.as_tensor(rng.integers(0, B.n, n), dtype=torch.int32, device="cuda")
+        vocab.grad = None
+        api.flowtree(vocab, tree, DA, DB, pa, pb, flows=F).sum().backward()
+        ref = api.Flows(tree, DA, DB, pa, pb)
+        api.flowtree_batch(tree, tree.points, DA, DB, ref.pair_a, ref.pair_b, flows=ref)
+        want = api.flowtree_backward(tree, DA, DB, ref, tree.points, torch.ones(n, device="cuda"))
+        assert torch.equal(vocab.grad, want)
+    assert tree.status() == 0
