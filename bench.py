@@ -654,7 +654,7 @@ def extras(args, tree, D, Q, q_h, db_h, pts, shift, batched_value, dev, pk, pk_k
             "exhaustive_flowtree_top10_kept_by_quadtree_top_k1": float(np.mean([len(set(e) & set(q_)) / TOPK
                                                                               for e, q_ in zip(ex, qi)])),
             "queries_checked": nx,
-            "stage": "centroid distances: FP32 centroids, cuBLAS SGEMM cross terms, top-k1 select (ft_mean_scan)"}
+            "stage": "centroid distances: FP32 centroids, tiled FP32 cross terms with the distance epilogue fused, radix select of the k1 smallest per query (ft_mean_scan)"}
     except Exception as ex:  # report, do not lose the main line
         out["text_mean_prefilter"] = {"error": "%s: %s" % (type(ex).__name__, ex)}
 

@@ -375,11 +375,12 @@ ft_status ft_exact_w1_batch(const float* vocab_dev, const ft_docs* a, const ft_d
  * distance between the mass-weighted centroids over the rows of vocab_dev
  * float32 [n_points][dim] (a lower bound on W1).  cand_ids_out_dev int32
  * [nq][k1] / cand_dist_out_dev float32 [nq][k1]: the k1 smallest per query,
- * ascending by (distance, document id).  FP32 throughout: the centroid cross
- * products are one cuBLAS SGEMM (FP32 math mode), the distance
- * sqrt(|c_q|^2 + |c_d|^2 - 2 c_q . c_d).  k1 <= min(n_db, 4096).
- * Allocation-free; not for use inside stream capture (cuBLAS may pick a
- * workspace of its own).
+ * ascending by (distance, document id).  FP32 throughout (the library's own
+ * tiled kernel: centroid cross products with the distance epilogue
+ * sqrt(|c_q|^2 + |c_d|^2 - 2 c_q . c_d) fused, then a radix select over each
+ * query's distance row).  k1 <= min(n_db, 4096); at most 65535 * 128
+ * queries per call.  Allocation-free: the centroids and the [nq][n_db]
+ * distance matrix live in the workspace.
  * ------------------------------------------------------------------------ */
 size_t ft_mean_scan_workspace_size(const ft_docs* queries, const ft_docs* db, int32_t k1);
 ft_status ft_mean_scan(const float* vocab_dev, const ft_docs* queries, const ft_docs* db, int32_t k1,

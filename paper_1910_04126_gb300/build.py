@@ -57,9 +57,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if force or jobs or not os.path.exists(LIB):
         tmp = LIB + ".tmp.%d" % os.getpid()
         libdir = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc()))), "lib64")
-        # cuBLAS for the plain FP32 GEMM of the mean-distance prefilter
-        cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-L", libdir, "-lcublas", "-Xlinker", "-rpath",
-               "-Xlinker", libdir]
+        cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-L", libdir, "-Xlinker", "-rpath", "-Xlinker", libdir]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n%s" % r.stderr)
