@@ -56,7 +56,10 @@ def flow_kernel(tree, a, b) -> str:
     if algo == _ffi.ALGO_AUTO:
         maxn = ((a.info.max_support + b.info.max_support + 31) // 32) * 32
         algo = _ffi.ALGO_BLOCKED if maxn <= _ffi.BLOCKED_MAX_ITEMS else _ffi.ALGO_WARP
-    return FLOW_KERNEL[algo]
+    name = FLOW_KERNEL[algo]
+    if algo == _ffi.ALGO_BLOCKED and a.info.max_support + b.info.max_support > _ffi.BLOCKED_WARP_ITEMS:
+        name += " + k_flowtree_team"  # the pairs beyond the warp's staging, a CTA each
+    return name
 
 
 def peaks():

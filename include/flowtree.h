@@ -227,13 +227,18 @@ ft_status ft_flowtree_plain(const ft_tree* t, const float* vocab_dev, const ft_d
  *                   per pair, one sweep with a stack of open tree nodes, its
  *                   per-position state as bit arrays in shared memory;
  *                   dim <= 8 only) or FT_ALGO_BLOCKED (a warp per pair, each
- *                   lane holding a contiguous block of up to 15 merged items
- *                   in registers: pairs of at most 480 merged items).
- *                   AUTO = BLOCKED when every pair of the batch can have at
- *                   most 480 merged items, else WARP; ft_flowtree_autotune
+ *                   lane owning a contiguous block of merged items in shared
+ *                   memory; pairs longer than the warp's staging are listed
+ *                   and then computed by a second launch with a CTA of 8
+ *                   warps per pair, up to 7,936 merged items).  AUTO =
+ *                   BLOCKED when the device can hold its buffers for the
+ *                   batch's longest pair, else WARP; ft_flowtree_autotune
  *                   picks among all three.
  *   warps_per_cta : warps per CTA (1..8).
- *   stage_items   : merged support items each warp stages on chip (WARP).
+ *   stage_items   : merged support items each warp stages on chip (WARP;
+ *                   BLOCKED: the warp's staging, rounded up to 32 x an odd
+ *                   number; 0 = 416 items, or less when every pair is
+ *                   shorter).
  *   stage_tables  : 1 = copy the vocabulary and the LCA table into shared
  *                   memory per CTA when they fit (at most 32 KiB); 0 = read
  *                   them through L1 (the default: one cached copy per SM

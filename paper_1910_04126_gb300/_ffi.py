@@ -32,7 +32,8 @@ class DocsInfo(C.Structure):
 
 
 ALGO_AUTO, ALGO_WARP, ALGO_THREAD, ALGO_BLOCKED = 0, 1, 2, 3
-BLOCKED_MAX_ITEMS = 992  # longest merged pair of the blocked form (31 items per lane)
+BLOCKED_MAX_ITEMS = 7936  # longest merged pair of the blocked form (a CTA of 256 threads, 31 items each)
+BLOCKED_WARP_ITEMS = 416  # the warp's default staging; longer pairs take a CTA each
 
 
 class FlowtreeConfig(C.Structure):

@@ -6,6 +6,7 @@
 
 #include "ft_flow.cuh"
 #include "ft_flow_blocked.cuh"
+#include "ft_flow_team.cuh"
 #include "ft_flow_thread.cuh"
 
 using namespace ftk;
@@ -14,7 +15,8 @@ namespace {
 
 constexpr int kDefaultWarps = 4;
 constexpr int kMaxStage = 2048;
-constexpr int kBlockedCap = 32 * 31;  // longest pair of the blocked form (31 items per lane)
+constexpr int kBlockedCap = 32 * 31;   // longest pair of a warp of the blocked form (31 items per lane)
+constexpr int kWarpCapDefault = 32 * 13; // the warp's default staging when longer pairs go to the team launch
 
 // A warp per pair, persistent: warps take `grab` consecutive queue entries at
 // a time.  Dynamic shared memory: [tables (if staged)] [one WarpBuf per warp].
@@ -87,12 +89,50 @@ __global__ void __launch_bounds__(256) k_flowtree_blocked(FlowCtx c, int grab, i
             float cost;
             if (n <= cap) {
                 cost = flowtree_pair_blocked<MODE, SAVE, PT16>(c, w, tb, pair, da, db);
+            } else if (c.long_list) {  // a CTA of the team launch takes it
+                if (lane == 0) c.long_list[atomicAdd(c.long_count, 1u)] = uint32_t(pair);
+                continue;
             } else {
                 if (lane == 0) ft_flag(c.status, FT_DEV_EOVERFLOW);
                 cost = __int_as_float(0x7fc00000);
             }
             if (lane == 0) c.cost_out[pair] = cost;
         }
+    }
+}
+
+// A CTA per pair (ft_flow_team.cuh) for the pairs the blocked warp form
+// listed as too long for its staging; persistent over that list.  Dynamic
+// shared memory: [tables (if staged)] [TeamBuf].
+template <int MODE, bool SAVE>
+__global__ void __launch_bounds__(kTeamThreads) k_flowtree_team(FlowCtx c, unsigned int* team_queue, int cap,
+                                                                int tables_bytes) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ TeamScratch ts;
+    const Tables tb = tables_bytes > 0 ? stage_tables(c, smem) : Tables{c.vocab, c.rmq};
+    const TeamBuf w = carve_teambuf(smem + tables_bytes, cap);
+    const unsigned n_long = *c.long_count;
+    for (;;) {
+        if (threadIdx.x == 0) ts.pair = atomicAdd(team_queue, 1u);
+        __syncthreads();
+        const unsigned q = unsigned(ts.pair);
+        __syncthreads();
+        if (q >= n_long) break;
+        const int64_t pair = int64_t(c.long_list[q]);
+        int64_t da, db;
+        if (!pair_docs(c, pair, &da, &db)) {  // cannot happen: the warp form checked the pair
+            if (threadIdx.x == 0) c.cost_out[pair] = __int_as_float(0x7fc00000);
+            continue;
+        }
+        const int n = int(c.a_ptr[da + 1] - c.a_ptr[da]) + int(c.b_ptr[db + 1] - c.b_ptr[db]);
+        float cost;
+        if (n <= cap) {
+            cost = flowtree_pair_team<MODE, SAVE>(c, w, ts, tb, pair, da, db);
+        } else {
+            if (threadIdx.x == 0) ft_flag(c.status, FT_DEV_EOVERFLOW);
+            cost = __int_as_float(0x7fc00000);
+        }
+        if (threadIdx.x == 0) c.cost_out[pair] = cost;
     }
 }
 
@@ -242,6 +282,11 @@ struct Plan {
     int64_t n_pairs = 0;
     int tables_bytes = 0;  // vocabulary + LCA table staged in shared memory (0 = read from global)
     void* kernel = nullptr;  // blocked form: the instantiation to launch
+    // blocked form, pairs longer than the warp's staging: a CTA per pair
+    int team_cap = 0;        // 0: no team launch
+    size_t team_smem = 0;
+    int team_blocks = 0;
+    void* team_kernel = nullptr;
     // thread algorithm: the lane-per-pair launch; cap, warps, blocks, smem
     // above then describe the warp-per-pair launch for its overflow pairs
     int tw = 0;            // words per bit array of a lane (positions up to the longest pair)
@@ -288,6 +333,17 @@ void* blocked_kernel(const ft_tree* t, int mode, bool save) {
     return blocked_pt16(t) ? blocked_fn<true>(mode, save) : blocked_fn<false>(mode, save);
 }
 
+void* team_kernel(int mode, bool save) {
+    switch (mode * 2 + (save ? 1 : 0)) {
+        case 0: return reinterpret_cast<void*>(&k_flowtree_team<0, false>);
+        case 1: return reinterpret_cast<void*>(&k_flowtree_team<0, true>);
+        case 2: return reinterpret_cast<void*>(&k_flowtree_team<1, false>);
+        case 3: return reinterpret_cast<void*>(&k_flowtree_team<1, true>);
+        case 4: return reinterpret_cast<void*>(&k_flowtree_team<2, false>);
+        default: return reinterpret_cast<void*>(&k_flowtree_team<2, true>);
+    }
+}
+
 void* persistent_kernel(int mode, bool save) {
     switch (mode * 2 + (save ? 1 : 0)) {
         case 0: return persistent_fn<0, false>();
@@ -305,15 +361,15 @@ int pick_mode(const ft_tree* t, const float* vocab) {
     return 2;
 }
 
-ft_status make_plan(const ft_tree* t, const ft_docs* a, const ft_docs* b, int64_t n_pairs, int mode, bool save,
-                    bool explicit_pairs, const ft_flowtree_config& cfg, Plan* p) {
+ft_status make_plan_algo(const ft_tree* t, const ft_docs* a, const ft_docs* b, int64_t n_pairs, int mode, bool save,
+                         bool explicit_pairs, const ft_flowtree_config& cfg, Plan* p) {
     p->mode = mode;
     p->n_pairs = n_pairs;
     p->warps = cfg.warps_per_cta > 0 ? cfg.warps_per_cta : kDefaultWarps;
     const int maxn = round32(std::max(a->max_support + b->max_support, 32));
     p->need_order = explicit_pairs && n_pairs > 1;
     const bool thread_ok = t->dim <= 8 && maxn <= kThreadMaxItems;
-    p->algo = cfg.algo != FT_ALGO_AUTO ? cfg.algo : (maxn <= kBlockedCap ? FT_ALGO_BLOCKED : FT_ALGO_WARP);
+    p->algo = cfg.algo;
     int dev = 0, max_smem = 0, sms = 0;
     FT_CUDA(cudaGetDevice(&dev));
     FT_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
@@ -337,8 +393,13 @@ ft_status make_plan(const ft_tree* t, const ft_docs* a, const ft_docs* b, int64_
         return FT_OK;
     }
     if (p->algo == FT_ALGO_BLOCKED) {
-        if (maxn > kBlockedCap) return FT_EUNSUPPORTED;
-        p->cap = 32 * ((maxn / 32) | 1);  // an odd number of items per lane
+        // the warp's staging: an odd number of items per lane, at most what the
+        // longest pair needs; by default 13 per lane (pairs up to 416 items),
+        // longer pairs go to a CTA each
+        const int need = 32 * ((maxn / 32) | 1);
+        int capw = cfg.stage_items > 0 ? 32 * (((cfg.stage_items + 31) / 32) | 1) : std::min(need, kWarpCapDefault);
+        capw = std::min(std::min(capw, need), kBlockedCap);
+        p->cap = capw;
         p->smem = size_t(p->tables_bytes) +
                   size_t(p->warps) * blockedbuf_bytes(p->cap, blocked_pt16(t), blocked_has_meta(blocked_pt16(t), save));
         if (p->smem > size_t(max_smem)) return FT_EUNSUPPORTED;
@@ -347,6 +408,16 @@ ft_status make_plan(const ft_tree* t, const ft_docs* a, const ft_docs* b, int64_
         FT_TRY(ft_prepare_kernel(p->kernel, p->warps * 32, p->smem, &bps));
         if (bps < 1) return FT_EUNSUPPORTED;
         p->blocks = sms * bps;
+        if (maxn > capw) {
+            p->team_cap = kTeamThreads * (((maxn + kTeamThreads - 1) / kTeamThreads) | 1);
+            p->team_smem = size_t(p->tables_bytes) + teambuf_bytes(p->team_cap);
+            if (p->team_smem + sizeof(TeamScratch) > size_t(max_smem)) return FT_EUNSUPPORTED;
+            p->team_kernel = team_kernel(mode, save);
+            int tbps = 0;
+            FT_TRY(ft_prepare_kernel(p->team_kernel, kTeamThreads, p->team_smem, &tbps));
+            if (tbps < 1) return FT_EUNSUPPORTED;
+            p->team_blocks = sms * tbps;
+        }
         return FT_OK;
     }
     int cap = cfg.stage_items > 0 ? round32(cfg.stage_items) : std::min(maxn, 512);
@@ -366,8 +437,24 @@ ft_status make_plan(const ft_tree* t, const ft_docs* a, const ft_docs* b, int64_
     return FT_OK;
 }
 
+// AUTO: the blocked form (warp per pair, with a CTA per pair beyond the
+// warp's staging) when the device can hold its buffers, else the compacting
+// warp form.
+ft_status make_plan(const ft_tree* t, const ft_docs* a, const ft_docs* b, int64_t n_pairs, int mode, bool save,
+                    bool explicit_pairs, const ft_flowtree_config& cfg, Plan* p) {
+    if (cfg.algo != FT_ALGO_AUTO) return make_plan_algo(t, a, b, n_pairs, mode, save, explicit_pairs, cfg, p);
+    ft_flowtree_config c2 = cfg;
+    c2.algo = FT_ALGO_BLOCKED;
+    const ft_status st = make_plan_algo(t, a, b, n_pairs, mode, save, explicit_pairs, c2, p);
+    if (st != FT_EUNSUPPORTED) return st;
+    *p = Plan();
+    c2.algo = FT_ALGO_WARP;
+    return make_plan_algo(t, a, b, n_pairs, mode, save, explicit_pairs, c2, p);
+}
+
 struct WsLayout {
-    unsigned int* queue;
+    unsigned int* queue;  // [0..1] pair counter, [2] long pairs listed, [3] long pairs taken
+    uint32_t* long_list;  // blocked form with a team launch: [n_pairs]
     uint32_t* gres;       // thread algorithm: residuals of partly matched items, per thread
     uint32_t* order;
     uint32_t* keys;
@@ -380,6 +467,7 @@ size_t layout(const Plan& p, void* base, WsLayout* out) {
     WsLayout l{};
     l.queue = w.take<unsigned int>(4);
     if (p.algo == FT_ALGO_THREAD) l.gres = w.take<uint32_t>(size_t(p.tblocks) * p.twarps * 32 * p.tmaxn);
+    if (p.team_cap > 0) l.long_list = w.take<uint32_t>(size_t(p.n_pairs));
     if (p.need_order) {
         l.order = w.take<uint32_t>(size_t(p.n_pairs));
         l.keys = w.take<uint32_t>(size_t(p.n_pairs));
@@ -438,6 +526,12 @@ ft_status launch_warps(const Plan& p, const FlowCtx& c, bool save, cudaStream_t 
     if (p.algo == FT_ALGO_BLOCKED) {
         void* args[] = {&cc, &g, &cap, &tbytes};
         FT_CUDA(cudaLaunchKernel(p.kernel, dim3(p.blocks), dim3(p.warps * 32), args, p.smem, s));
+        if (p.team_cap > 0) {
+            unsigned int* tq = c.queue + 3;
+            int tcap = p.team_cap;
+            void* targs[] = {&cc, &tq, &tcap, &tbytes};
+            FT_CUDA(cudaLaunchKernel(p.team_kernel, dim3(p.team_blocks), dim3(kTeamThreads), targs, p.team_smem, s));
+        }
         return FT_OK;
     }
     void* fn = persistent_kernel(p.mode, save);
@@ -447,7 +541,7 @@ ft_status launch_warps(const Plan& p, const FlowCtx& c, bool save, cudaStream_t 
 }
 
 ft_status launch_persistent(const Plan& p, const WsLayout& l, FlowCtx c, bool save, cudaStream_t s) {
-    FT_CUDA(cudaMemsetAsync(c.queue, 0, 8, s));
+    FT_CUDA(cudaMemsetAsync(c.queue, 0, 16, s));
     if (p.algo != FT_ALGO_THREAD) return launch_warps(p, c, save, s);
     void* fn = thread_kernel(save);
     int tw = p.tw, tbytes = p.tables_bytes, nmax = p.tmaxn;
@@ -473,6 +567,10 @@ ft_status run_batch(const ft_tree* t, const float* vocab, const ft_docs* a, cons
     FlowCtx c = make_ctx(t, vocab, a, b, pa, pb, n_pairs, cost_out);
     c.queue = l.queue;
     c.gscratch = l.gscratch;
+    if (p.team_cap > 0) {
+        c.long_list = l.long_list;
+        c.long_count = l.queue + 2;
+    }
     c.gscratch_items = p.gscratch_items;
     c.gscratch_warp_bytes = p.gscratch_warp_bytes;
     if (p.need_order) {
@@ -606,9 +704,11 @@ extern "C" ft_status ft_flowtree_autotune(ft_tree* t, const float* vocab_dev, co
         for (int w : warps)
             for (int st : {0, 1}) cands.push_back({w, cap, FT_ALGO_WARP, st});
     }
-    if (maxn <= kBlockedCap) {
-        for (int w : {2, 3, 4, 6, 8})
-            for (int st : {0, 1}) cands.push_back({w, 0, FT_ALGO_BLOCKED, st});
+    // the blocked form: warps per CTA x the warp's staging (0 = default; longer pairs take a CTA each)
+    for (int w : {2, 3, 4, 6, 8}) {
+        for (int st : {0, 1}) cands.push_back({w, 0, FT_ALGO_BLOCKED, st});
+        for (int stage : {224, 352, 480, 608})
+            if (stage < maxn) cands.push_back({w, stage, FT_ALGO_BLOCKED, 0});
     }
     if (t->dim <= 8 && maxn <= kThreadMaxItems) {
         // lane per pair: warps per block x item buffer entries per lane

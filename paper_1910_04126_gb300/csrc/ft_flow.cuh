@@ -70,6 +70,9 @@ struct FlowCtx {
     uint32_t* f_f;
     uint8_t* f_depth;
     float* f_dist;
+    // blocked form: pairs beyond the warp's staging, left to the CTA-per-pair launch
+    uint32_t* long_list;
+    unsigned int* long_count;
     // long-pair scratch
     uint8_t* gscratch;
     size_t gscratch_warp_bytes;

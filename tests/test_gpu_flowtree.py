@@ -159,12 +159,14 @@ def test_plain_form_equals_batched(name):
 
 @pytest.mark.parametrize("cap", [32, 64, 96])
 def test_long_pairs_use_workspace_staging(cap):
-    # Pairs longer than the on-chip staging take the workspace path.
+    # The compacting warp form: pairs longer than its on-chip staging take the workspace path, bitwise equal
+    # to the same form with enough staging.
     pts, L, shift, db, q = CASES["d300"]
     tree, otree = build_both(pts, L, shift)
     Dd, Dq = api.Docs.from_csr(tree, db), api.Docs.from_csr(tree, q)
+    tree.set_config(0, 0, 1)
     ref = api.flowtree_batch(tree, tree.points, Dq, Dd).cpu().numpy()
-    tree.set_config(2, cap)
+    tree.set_config(2, cap, 1)
     got = api.flowtree_batch(tree, tree.points, Dq, Dd).cpu().numpy()
     assert np.array_equal(got, ref)
     Sd, Sq = oracle_supports(otree, db), oracle_supports(otree, q)
@@ -246,4 +248,40 @@ def test_thread_form_block_shapes(name, warps):
         ref = sorted(zip(ia.tolist(), ib.tolist(), f.tolist(), dep.tolist()))
         g = got_f[i]
         assert sorted(zip(g[0].tolist(), g[1].tolist(), g[2].tolist(), g[3].tolist())) == ref, i
+    assert tree.status() == 0
+
+
+@pytest.mark.parametrize("algo,stage", [(0, 0), (3, 224)])
+def test_long_pairs_cta_form_bit_exact(algo, stage):
+    """Supports of 2,000 points on both sides (the scale workload's longest documents) mixed with short ones: the
+    pairs beyond the warp's staging go to a CTA each (the default staging, or one forced down to 224 items), and
+    their saved flows are bit-exact against the oracle, their values within 1e-5."""
+    rng = np.random.default_rng(30)
+    pts = rng.random((6000, 2)).astype(np.float32)
+    shift = synth.random_shift(2, 31)
+    lens = np.array([2000, 2000, 1500, 40, 900, 20, 300, 2000, 64, 1200])
+    docs = synth.csr_from_lists([rng.choice(6000, s, replace=False) for s in lens],
+                                [rng.random(s).astype(np.float32) + 0.1 for s in lens])
+    tree, otree = build_both(pts, 12, shift)
+    tree.set_config(0, stage, algo)
+    D = api.Docs.from_csr(tree, docs)
+    S = oracle_supports(otree, docs)
+    n = docs.n
+    pa = np.repeat(np.arange(n), n)
+    pb = np.tile(np.arange(n), n)
+    flows = api.Flows(tree, D, D, pa, pb)
+    got = api.flowtree_batch(tree, tree.points, D, D, flows.pair_a, flows.pair_b, flows=flows).cpu().numpy()
+    ref = _oracle_costs(otree, pts, S, S, pa, pb)
+    np.testing.assert_allclose(got.astype(np.float64), ref, rtol=REL, atol=1e-30)
+    ex = flows.export()
+    for i in range(len(pa)):
+        ia, ib, f, dep = otree.flow(*S.doc(pa[i]), *S.doc(pb[i]))
+        want = sorted(zip(ia.tolist(), ib.tolist(), f.tolist(), dep.tolist()))
+        g = ex[i]
+        assert sorted(zip(g[0].tolist(), g[1].tolist(), g[2].tolist(), g[3].tolist())) == want, i
+    # the cross-product form of the same documents (no saved flows), and a second run gives the same bits
+    c1 = api.flowtree_batch(tree, tree.points, D, D).cpu().numpy()
+    c2 = api.flowtree_batch(tree, tree.points, D, D).cpu().numpy()
+    np.testing.assert_allclose(c1.astype(np.float64), ref, rtol=REL, atol=1e-30)
+    assert np.array_equal(c1, c2)
     assert tree.status() == 0
