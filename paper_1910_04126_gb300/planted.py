@@ -17,7 +17,8 @@ document against all s (N - s) single swaps; "success" = the planted
 document's score is strictly the smallest (a tie is a failure: the method
 cannot tell the documents apart); the rate at which it is among the
 minimisers is reported too.  For Flowtree this is a necessary condition for
-success over the whole dataset.
+success over the whole dataset.  A second reading ranks the planted document
+against a uniform sample of the dataset (random s-subsets of X) instead.
 
 Every repetition draws a new instance and a new random shift of the tree;
 both scores come from the library (ft_quadtree_l1_dense, ft_flowtree_batch).
@@ -33,8 +34,12 @@ from . import api, synth
 
 
 def run(n_points_list, dim: int = 10, s: int = 10, eps: float = 0.25, reps: int = 100, seed: int = 0,
-        levels: int = 12, device: str = "cuda") -> dict:
-    """Success fractions of Quadtree and Flowtree for every N in n_points_list."""
+        levels: int = 12, device: str = "cuda", competitors: str = "swaps", n_random: int = 2000) -> dict:
+    """Success fractions of Quadtree and Flowtree for every N in n_points_list.
+
+    competitors: "swaps" -- every single swap of the planted support (the
+    documents that decide the theorem's events); "random" -- n_random
+    uniformly random s-subsets, a sample of the model's dataset."""
     dev = torch.device(device)
     out = []
     for n in n_points_list:
@@ -45,7 +50,10 @@ def run(n_points_list, dim: int = 10, s: int = 10, eps: float = 0.25, reps: int 
             inst_seed = 1_000_003 * (seed + 1) + 7919 * int(n) + r
             pts, support, query = synth.planted_instance(int(n), dim, s, eps, inst_seed)
             shift = synth.random_shift(dim, inst_seed + 17)
-            cand = synth.single_swap_docs(support, int(n))
+            if competitors == "swaps":
+                cand = synth.single_swap_docs(support, int(n))
+            else:
+                cand = synth.random_subset_docs(support, int(n), n_random, inst_seed + 29)
             qdoc = synth.csr_from_lists([query])
             tree = api.Tree(torch.as_tensor(pts, device=dev), levels, shift)
             D, Q = api.Docs.from_csr(tree, cand), api.Docs.from_csr(tree, qdoc)
@@ -64,11 +72,12 @@ def run(n_points_list, dim: int = 10, s: int = 10, eps: float = 0.25, reps: int 
             status = tree.status()
             if status != 0:
                 raise RuntimeError("device status %d in the planted experiment (N=%d, rep %d)" % (status, n, r))
-        out.append({"n_points": int(n), "candidates_per_query": 1 + s * (int(n) - s),
+        out.append({"n_points": int(n), "candidates_per_query": cand.n,
                     "quadtree_success": ok_qt / reps, "flowtree_success": ok_ft / reps,
                     "quadtree_among_minimizers": tie_qt / reps, "flowtree_among_minimizers": tie_ft / reps,
                     "pairs_scored": pairs, "gpu_seconds": gpu_s})
-    return {"dim": dim, "s": s, "eps": eps, "reps": reps, "levels": levels, "results": out}
+    return {"dim": dim, "s": s, "eps": eps, "reps": reps, "levels": levels, "competitors": competitors,
+            "results": out}
 
 
 if __name__ == "__main__":
@@ -82,5 +91,6 @@ if __name__ == "__main__":
     ap.add_argument("--eps", type=float, default=0.25)
     ap.add_argument("--reps", type=int, default=100)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--competitors", choices=["swaps", "random"], default="swaps")
     a = ap.parse_args()
-    print(json.dumps(run(a.n, a.dim, a.s, a.eps, a.reps, a.seed)))
+    print(json.dumps(run(a.n, a.dim, a.s, a.eps, a.reps, a.seed, competitors=a.competitors)))

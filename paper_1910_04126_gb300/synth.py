@@ -345,6 +345,28 @@ def planted_instance(n_points: int, dim: int, s: int, eps: float, seed: int):
     return pts, support.astype(np.int64), np.arange(n_points, n_points + s, dtype=np.int64)
 
 
+def random_subset_docs(support: np.ndarray, n_points: int, n_docs: int, seed: int) -> Docs:
+    """The planted support (document 0) and n_docs uniformly random s-subsets of
+    the ground set (documents 1 .. n_docs), drawn from the model's dataset of all
+    s-subsets; a draw equal to the planted support is redrawn.  Uniform
+    weights."""
+    support = np.asarray(support, dtype=np.int64)
+    s = len(support)
+    rng = np.random.default_rng(seed)
+    planted = np.sort(support)
+    out = np.empty((n_docs, s), dtype=np.int64)
+    todo = np.arange(n_docs)
+    while len(todo):  # draw whole rows, redraw the ones with a repeated point or equal to the planted support
+        d = rng.integers(0, n_points, (len(todo), s))
+        srt = np.sort(d, axis=1)
+        bad = (np.diff(srt, axis=1) == 0).any(axis=1) | (srt == planted).all(axis=1)
+        out[todo[~bad]] = d[~bad]
+        todo = todo[bad]
+    words = np.concatenate([support[None, :], out]).astype(np.int32)
+    rp = np.arange(n_docs + 2, dtype=np.int64) * s
+    return Docs(rp, words.reshape(-1), np.ones(words.size, np.float32))
+
+
 def single_swap_docs(support: np.ndarray, n_points: int) -> Docs:
     """The planted support (document 0) and every support that differs from it
     in one point: x_k replaced by any x' of the ground set outside the support

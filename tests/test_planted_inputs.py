@@ -45,3 +45,15 @@ def test_single_swap_docs():
     for d in docs[1:]:
         assert len(set(d)) == 3 and len(set(d) & {5, 2, 9}) == 2
     assert np.all(D.weight == 1.0)
+
+
+def test_random_subset_competitors():
+    support = np.array([3, 17, 5, 40])
+    d = synth.random_subset_docs(support, 50, 300, seed=1)
+    assert d.n == 301
+    assert np.array_equal(d.word[:4], support)
+    planted = np.sort(support)
+    for i in range(1, d.n):
+        w = d.word[d.row_ptr[i]:d.row_ptr[i + 1]]
+        assert len(w) == 4 and len(set(w.tolist())) == 4 and w.min() >= 0 and w.max() < 50
+        assert not np.array_equal(np.sort(w), planted)
