@@ -251,8 +251,10 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_qt_scan(ScanArgs a) {
     }
 }
 
-// Per row: the k smallest of n unique u64 keys, ascending, by an 8-bit
-// radix select (MSB first) followed by a bitonic sort of the k survivors.
+// Per row: the k smallest of n unique u64 keys, ascending, by a radix select
+// over 11-bit digits (most significant first) that stops as soon as the keys
+// at or below the current prefix fit the candidate buffer (or at the exact
+// k-th key), followed by a bitonic sort of the survivors.
 // Quadtree keys (F32 = false): ids_out = low 24 bits, l1_out = key >> 24.
 // Value keys (F32 = true): key = (float bits << 32) | column, ids_out = low 32
 // bits, val_out = the float.
@@ -260,57 +262,97 @@ template <bool F32>
 __global__ void __launch_bounds__(SEL_THREADS) k_select_u64(const uint64_t* __restrict__ keys, int64_t n, int k,
                                                             int32_t* __restrict__ ids_out, int64_t* __restrict__ l1_out,
                                                             float* __restrict__ val_out, uint32_t* status) {
-    __shared__ uint32_t hist[256];
+    __shared__ uint32_t hist[2048];
     __shared__ uint64_t cand[MAX_K1];
     __shared__ uint64_t prefix_s, mask_s;
-    __shared__ int krem_s, cnt_s;
+    __shared__ int krem_s, cnt_s, below_s, eq_s;
     const uint64_t* row = keys + int64_t(blockIdx.x) * n;
     if (threadIdx.x == 0) {
         prefix_s = 0;
         mask_s = 0;
         krem_s = k;
         cnt_s = 0;
+        below_s = 0;
+        eq_s = n < int64_t(0x7FFFFFFF) ? int(n) : 0x7FFFFFFF;
     }
     __syncthreads();
-    for (int dg = 7; dg >= 0; --dg) {
-        for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+    bool exact = true;
+    for (int dg = 0; dg < 6; ++dg) {
+        if (below_s + eq_s <= MAX_K1) {
+            exact = false;  // every key at or below the prefix fits the buffer
+            break;
+        }
+        // digits: bits 63..53, 52..42, 41..31, 30..20, 19..9, 8..0
+        const int sh = dg < 5 ? 53 - 11 * dg : 0, nb = dg < 5 ? 2048 : 512;
+        for (int i = threadIdx.x; i < nb; i += blockDim.x) hist[i] = 0;
         __syncthreads();
         const uint64_t prefix = prefix_s, mask = mask_s;
         // eight independent key loads in flight per thread (the row streams
-        // from L2/HBM once per digit)
+        // from L2/HBM once per digit); the loop is warp-uniform so that a warp
+        // whose counted keys share one bucket adds them with one atomic
+        const int lane = threadIdx.x & 31;
         const int64_t step = int64_t(blockDim.x) * 8;
-        for (int64_t i0 = threadIdx.x; i0 < n; i0 += step) {
+        for (int64_t i0 = threadIdx.x - lane; i0 < n; i0 += step) {
             uint64_t kv[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                const int64_t i = i0 + int64_t(u) * blockDim.x;
+                const int64_t i = i0 + lane + int64_t(u) * blockDim.x;
                 kv[u] = i < n ? row[i] : ~uint64_t(0);
             }
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                const int64_t i = i0 + int64_t(u) * blockDim.x;
-                if (i < n && (kv[u] & mask) == prefix) atomicAdd(&hist[(kv[u] >> (8 * dg)) & 255u], 1u);
+                const int64_t i = i0 + lane + int64_t(u) * blockDim.x;
+                const bool in = i < n && (kv[u] & mask) == prefix;
+                const uint32_t bk = uint32_t(kv[u] >> sh) & uint32_t(nb - 1);
+                const unsigned act = __ballot_sync(0xFFFFFFFFu, in);
+                if (act == 0) continue;
+                const int leader = __ffs(act) - 1;
+                const uint32_t lb = __shfl_sync(0xFFFFFFFFu, bk, leader);
+                const unsigned same = __ballot_sync(0xFFFFFFFFu, in && bk == lb);
+                if (same == act) {
+                    if (lane == leader) atomicAdd(&hist[lb], unsigned(__popc(act)));
+                } else if (in) {
+                    atomicAdd(&hist[bk], 1u);
+                }
             }
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            int krem = krem_s;
-            int b = 0;
-            for (; b < 256; ++b) {
-                if (int(hist[b]) >= krem) break;
-                krem -= int(hist[b]);
+        // warp 0 finds the bucket of the krem-th counted key: lane sums over
+        // nb/32 buckets, a warp scan, then the owning lane walks its buckets
+        if (threadIdx.x < 32) {
+            const int per = nb >> 5;
+            int sum = 0;
+            for (int j = 0; j < per; ++j) sum += int(hist[lane * per + j]);
+            int inc = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+                if (lane >= o) inc += t;
             }
-            if (b == 256) {  // fewer than k keys: cannot happen for k <= n
-                ft_flag(status, FT_DEV_EINVAL);
-                b = 255;
+            const int krem0 = krem_s;
+            const unsigned hit = __ballot_sync(0xFFFFFFFFu, inc >= krem0);
+            const int owner = hit ? __ffs(hit) - 1 : 31;
+            if (lane == owner) {
+                if (!hit) ft_flag(status, FT_DEV_EINVAL);  // fewer than k keys: cannot happen for k <= n
+                int krem = krem0 - (inc - sum), below = below_s + (inc - sum);
+                int b = lane * per;
+                for (; b < lane * per + per - 1; ++b) {
+                    if (int(hist[b]) >= krem) break;
+                    krem -= int(hist[b]);
+                    below += int(hist[b]);
+                }
+                krem_s = krem;
+                below_s = below;
+                eq_s = int(hist[b]);
+                prefix_s = prefix | (uint64_t(b) << sh);
+                mask_s = mask | (uint64_t(nb - 1) << sh);
             }
-            krem_s = krem;
-            prefix_s = prefix | (uint64_t(b) << (8 * dg));
-            mask_s = mask | (uint64_t(255) << (8 * dg));
         }
         __syncthreads();
     }
-    const uint64_t thr = prefix_s;  // the k-th smallest key
+    // exact: the k-th smallest key; else every key whose digits so far are at
+    // most the prefix (fewer than MAX_K1 of them)
+    const uint64_t thr = exact ? prefix_s : (prefix_s | ~mask_s);
     for (int64_t i0 = threadIdx.x; i0 < n; i0 += int64_t(blockDim.x) * 8) {
         uint64_t kv[8];
 #pragma unroll
@@ -327,9 +369,11 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_u64(const uint64_t* __re
         }
     }
     __syncthreads();
+    // exact: cnt == k; else k <= cnt <= MAX_K1 (MAX_K1 is a power of two)
+    const int cnt = min(cnt_s, MAX_K1);
     int m = 1;
-    while (m < k) m <<= 1;
-    for (int i = k + threadIdx.x; i < m; i += blockDim.x) cand[i] = ~uint64_t(0);
+    while (m < cnt || m < k) m <<= 1;
+    for (int i = cnt + threadIdx.x; i < m; i += blockDim.x) cand[i] = ~uint64_t(0);
     __syncthreads();
     for (int size = 2; size <= m; size <<= 1) {
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
