@@ -609,7 +609,8 @@ def extras(args, tree, D, Q, q_h, db_h, pts, shift, batched_value, dev, pk, pk_k
                       "ms_per_step": fb_ms, "backward_ms": b_ms,
                       "path": "torch.autograd: api.flowtree(vocab, ...).sum().backward(), caller-held flows",
                       "launch_config": {"warps_per_cta": tuned_fb[0], "stage_items": tuned_fb[1],
-                                        "algo": ALGO_NAMES[tuned_fb[2]], "picked_by": "ft_flowtree_autotune"},
+                                        "algo": ALGO_NAMES[tuned_fb[2]], "deep_loads": tuned_fb[4],
+                                        "picked_by": "ft_flowtree_autotune"},
                       "raw_api_ms_per_step": raw_ms,
                       "rebinding_flows": {"value": npairs / (fb_rebind_ms * 1e-3), "ms_per_step": fb_rebind_ms,
                                           "note": "Flows.with_capacity rebound every step (pairs may change)"},

@@ -243,6 +243,14 @@ ft_status ft_flowtree_plain(const ft_tree* t, const float* vocab_dev, const ft_d
  *                   memory per CTA when they fit (at most 32 KiB); 0 = read
  *                   them through L1 (the default: one cached copy per SM
  *                   leaves more shared memory for resident warps).
+ *   deep_loads    : WARP with dim > 8 (pricing by 8-lane groups): 1 = the
+ *                   build of the kernel that may use up to 255 registers per
+ *                   thread, so that a warp's pricing rounds keep more row
+ *                   loads in flight at the cost of resident warps: for
+ *                   batches too small to fill the GPU, whose time is the
+ *                   longest pairs' latency; 0 = the occupancy build (the
+ *                   default).  Ignored by the other forms and for dim <= 8.
+ *                   Both builds compute the same values bit for bit.
  * ft_flowtree_autotune times a few configurations on the given pairs (with
  * CUDA events on `stream`) and installs the fastest for this tree. */
 #define FT_ALGO_AUTO 0
@@ -254,6 +262,7 @@ typedef struct {
     int32_t stage_items;
     int32_t algo;
     int32_t stage_tables;
+    int32_t deep_loads;
 } ft_flowtree_config;
 ft_status ft_flowtree_set_config(ft_tree* t, const ft_flowtree_config* cfg);
 ft_status ft_flowtree_get_config(const ft_tree* t, ft_flowtree_config* cfg);

@@ -38,7 +38,7 @@ BLOCKED_WARP_ITEMS = 416  # the warp's default staging; longer pairs take a CTA 
 
 class FlowtreeConfig(C.Structure):
     _fields_ = [("warps_per_cta", C.c_int32), ("stage_items", C.c_int32), ("algo", C.c_int32),
-                ("stage_tables", C.c_int32)]
+                ("stage_tables", C.c_int32), ("deep_loads", C.c_int32)]
 
 
 vp = C.c_void_p

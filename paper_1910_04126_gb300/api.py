@@ -97,13 +97,15 @@ class Tree:
         return int(_ffi.load().ft_tree_status(self._h, _stream(stream)))
 
     def get_config(self):
-        """(warps_per_cta, stage_items, algo, stage_tables); 0 = default."""
+        """(warps_per_cta, stage_items, algo, stage_tables, deep_loads); 0 = default."""
         cfg = _ffi.FlowtreeConfig()
         check(_ffi.load().ft_flowtree_get_config(self._h, C.byref(cfg)), "ft_flowtree_get_config")
-        return int(cfg.warps_per_cta), int(cfg.stage_items), int(cfg.algo), int(cfg.stage_tables)
+        return (int(cfg.warps_per_cta), int(cfg.stage_items), int(cfg.algo), int(cfg.stage_tables),
+                int(cfg.deep_loads))
 
-    def set_config(self, warps_per_cta: int = 0, stage_items: int = 0, algo: int = 0, stage_tables: int = 0):
-        cfg = _ffi.FlowtreeConfig(warps_per_cta, stage_items, algo, stage_tables)
+    def set_config(self, warps_per_cta: int = 0, stage_items: int = 0, algo: int = 0, stage_tables: int = 0,
+                   deep_loads: int = 0):
+        cfg = _ffi.FlowtreeConfig(warps_per_cta, stage_items, algo, stage_tables, deep_loads)
         check(_ffi.load().ft_flowtree_set_config(self._h, C.byref(cfg)), "ft_flowtree_set_config")
 
     # -- checkpoint / resume ---------------------------------------------------
@@ -318,7 +320,8 @@ def flowtree_autotune(tree: Tree, vocab: torch.Tensor, a: Docs, b: Docs, pair_a=
     code = lib.ft_flowtree_autotune(tree.handle, _ptr(vocab), a.handle, b.handle, _ptr(pa), _ptr(pb), n_pairs,
                                     _ptr(scratch), _ptr(ws), ws.numel(), _stream(stream), C.byref(cfg))
     check(code, "ft_flowtree_autotune")
-    return int(cfg.warps_per_cta), int(cfg.stage_items), int(cfg.algo), int(cfg.stage_tables)
+    return (int(cfg.warps_per_cta), int(cfg.stage_items), int(cfg.algo), int(cfg.stage_tables),
+            int(cfg.deep_loads))
 
 
 def flowtree_backward(tree: Tree, a: Docs, b: Docs, flows: Flows, vocab: torch.Tensor, grad_cost: torch.Tensor,

@@ -21,7 +21,7 @@ constexpr int kWarpCapDefault = 32 * 13; // the warp's default staging when long
 // A warp per pair, persistent: warps take `grab` consecutive queue entries at
 // a time.  Dynamic shared memory: [tables (if staged)] [one WarpBuf per warp].
 template <int MODE, bool SAVE>
-__global__ void __launch_bounds__(256) k_flowtree_persistent(FlowCtx c, int cap, int grab, int tables_bytes) {
+__device__ __forceinline__ void persistent_body(const FlowCtx& c, int cap, int grab, int tables_bytes) {
     extern __shared__ __align__(16) uint8_t smem[];
     const int warp = int(threadIdx.x >> 5);
     const unsigned lane = lane_id();
@@ -58,6 +58,23 @@ __global__ void __launch_bounds__(256) k_flowtree_persistent(FlowCtx c, int cap,
             if (lane == 0) c.cost_out[pair] = cost;
         }
     }
+}
+
+// The occupancy build: the compiler keeps registers low enough for many
+// resident warps (throughput-bound batches: the row gathers of many pairs
+// overlap across warps).
+template <int MODE, bool SAVE>
+__global__ void __launch_bounds__(256) k_flowtree_persistent(FlowCtx c, int cap, int grab, int tables_bytes) {
+    persistent_body<MODE, SAVE>(c, cap, grab, tables_bytes);
+}
+
+// The deep-loads build (8-lane-group pricing only): one resident CTA is all
+// the compiler must allow, so a warp keeps its pricing rounds' row loads in
+// registers together; for batches too small to fill the GPU, whose time is
+// the longest pairs' latency on their warps.
+template <int MODE, bool SAVE>
+__global__ void __launch_bounds__(256, 1) k_flowtree_persistent_deep(FlowCtx c, int cap, int grab, int tables_bytes) {
+    persistent_body<MODE, SAVE>(c, cap, grab, tables_bytes);
 }
 
 // A warp per pair, register-blocked (ft_flow_blocked.cuh), persistent.
@@ -281,6 +298,7 @@ struct Plan {
     bool need_order = false;
     int64_t n_pairs = 0;
     int tables_bytes = 0;  // vocabulary + LCA table staged in shared memory (0 = read from global)
+    bool deep = false;     // warp form: the deep-loads build
     void* kernel = nullptr;  // blocked form: the instantiation to launch
     // blocked form, pairs longer than the warp's staging: a CTA per pair
     int team_cap = 0;        // 0: no team launch
@@ -344,7 +362,15 @@ void* team_kernel(int mode, bool save) {
     }
 }
 
-void* persistent_kernel(int mode, bool save) {
+void* persistent_kernel(int mode, bool save, bool deep) {
+    if (deep && mode >= 1) {
+        switch ((mode - 1) * 2 + (save ? 1 : 0)) {
+            case 0: return reinterpret_cast<void*>(&k_flowtree_persistent_deep<1, false>);
+            case 1: return reinterpret_cast<void*>(&k_flowtree_persistent_deep<1, true>);
+            case 2: return reinterpret_cast<void*>(&k_flowtree_persistent_deep<2, false>);
+            default: return reinterpret_cast<void*>(&k_flowtree_persistent_deep<2, true>);
+        }
+    }
     switch (mode * 2 + (save ? 1 : 0)) {
         case 0: return persistent_fn<0, false>();
         case 1: return persistent_fn<0, true>();
@@ -425,7 +451,8 @@ ft_status make_plan_algo(const ft_tree* t, const ft_docs* a, const ft_docs* b, i
     p->cap = cap;
     p->smem = size_t(p->tables_bytes) + size_t(p->warps) * warpbuf_bytes(cap);
     if (p->smem > size_t(max_smem)) return FT_EUNSUPPORTED;
-    void* fn = persistent_kernel(mode, save);
+    p->deep = cfg.deep_loads != 0 && mode >= 1;
+    void* fn = persistent_kernel(mode, save, p->deep);
     int bps = 0;
     FT_TRY(ft_prepare_kernel(fn, p->warps * 32, p->smem, &bps));
     if (bps < 1) return FT_EUNSUPPORTED;
@@ -534,7 +561,7 @@ ft_status launch_warps(const Plan& p, const FlowCtx& c, bool save, cudaStream_t 
         }
         return FT_OK;
     }
-    void* fn = persistent_kernel(p.mode, save);
+    void* fn = persistent_kernel(p.mode, save, p.deep);
     void* args[] = {&cc, &cap, &g, &tbytes};
     FT_CUDA(cudaLaunchKernel(fn, dim3(p.blocks), dim3(p.warps * 32), args, p.smem, s));
     return FT_OK;
@@ -702,19 +729,21 @@ extern "C" ft_status ft_flowtree_autotune(ft_tree* t, const float* vocab_dev, co
     for (int cap : caps) {
         if (cap > maxn || cap > kMaxStage) continue;
         for (int w : warps)
-            for (int st : {0, 1}) cands.push_back({w, cap, FT_ALGO_WARP, st});
+            for (int st : {0, 1}) cands.push_back({w, cap, FT_ALGO_WARP, st, 0});
+        if (t->dim > 8)  // the deep-loads build (8-lane-group pricing)
+            for (int w : {2, 4, 7}) cands.push_back({w, cap, FT_ALGO_WARP, 0, 1});
     }
     // the blocked form: warps per CTA x the warp's staging (0 = default; longer pairs take a CTA each)
     for (int w : {2, 3, 4, 6, 8}) {
-        for (int st : {0, 1}) cands.push_back({w, 0, FT_ALGO_BLOCKED, st});
+        for (int st : {0, 1}) cands.push_back({w, 0, FT_ALGO_BLOCKED, st, 0});
         for (int stage : {224, 352, 480, 608})
-            if (stage < maxn) cands.push_back({w, stage, FT_ALGO_BLOCKED, 0});
+            if (stage < maxn) cands.push_back({w, stage, FT_ALGO_BLOCKED, 0, 0});
     }
     if (t->dim <= 8 && maxn <= kThreadMaxItems) {
         // lane per pair: warps per block x item buffer entries per lane
-        for (int w : {2, 4, 8}) cands.push_back({w, 0, FT_ALGO_THREAD, 0});
+        for (int w : {2, 4, 8}) cands.push_back({w, 0, FT_ALGO_THREAD, 0, 0});
     }
-    if (cands.empty()) cands.push_back({kDefaultWarps, std::min(maxn, 512), FT_ALGO_WARP, 0});
+    if (cands.empty()) cands.push_back({kDefaultWarps, std::min(maxn, 512), FT_ALGO_WARP, 0, 0});
     cudaEvent_t e0, e1;
     FT_CUDA(cudaEventCreate(&e0));
     FT_CUDA(cudaEventCreate(&e1));

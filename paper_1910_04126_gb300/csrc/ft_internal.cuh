@@ -63,7 +63,7 @@ struct ft_tree {
     uint8_t* d_chain = nullptr;           // [n]   deepest depth at which rank r shares a cell
     uint32_t* d_node_id = nullptr;        // [L][n] dense node id of rank r at depth k (row k-1)
     uint32_t* d_status = nullptr;         // device status word
-    ft_flowtree_config cfg{0, 0, 0, 0};
+    ft_flowtree_config cfg{0, 0, 0, 0, 0};
 };
 
 struct ft_docs {

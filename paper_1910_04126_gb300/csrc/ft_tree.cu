@@ -393,7 +393,8 @@ extern "C" ft_status ft_tree_status(const ft_tree* t, void* stream) {
 extern "C" ft_status ft_flowtree_set_config(ft_tree* t, const ft_flowtree_config* cfg) {
     if (!t || !cfg) return FT_EINVAL;
     if (cfg->warps_per_cta < 0 || cfg->warps_per_cta > 8 || cfg->stage_items < 0 || cfg->stage_items > 16384 ||
-        cfg->algo < FT_ALGO_AUTO || cfg->algo > FT_ALGO_BLOCKED || cfg->stage_tables < 0 || cfg->stage_tables > 1)
+        cfg->algo < FT_ALGO_AUTO || cfg->algo > FT_ALGO_BLOCKED || cfg->stage_tables < 0 || cfg->stage_tables > 1 ||
+        cfg->deep_loads < 0 || cfg->deep_loads > 1)
         return FT_EINVAL;
     if (cfg->algo == FT_ALGO_THREAD && t->dim > 8) return FT_EUNSUPPORTED;
     t->cfg = *cfg;

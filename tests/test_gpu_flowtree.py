@@ -285,3 +285,39 @@ def test_long_pairs_cta_form_bit_exact(algo, stage):
     np.testing.assert_allclose(c1.astype(np.float64), ref, rtol=REL, atol=1e-30)
     assert np.array_equal(c1, c2)
     assert tree.status() == 0
+
+
+@pytest.mark.parametrize("name", ["d300", "d30"])
+def test_deep_loads_build_same_values(name):
+    """The warp form's deep-loads build (more registers per thread, the pricing rounds' row loads in flight
+    together) computes the same costs and saved flows (pairs, flows, depths, distances) bit for bit as the
+    occupancy build, over long pairs in the global staging too; the costs stay within 1e-5 of the oracle."""
+    pts, L, shift, db, q = CASES[name]
+    tree, otree = build_both(pts, L, shift)
+    Dd = api.Docs.from_csr(tree, db)
+    rng = np.random.default_rng(21)
+    n = 300
+    pa = rng.integers(0, db.n, n)
+    pb = rng.integers(0, db.n, n)
+    res = []
+    for deep in (0, 1):
+        for cap in (0, 64):  # 64: most pairs exceed the staging and run from the workspace
+            tree.set_config(4, cap, 1, 0, deep)
+            assert tree.get_config() == (4, cap, 1, 0, deep)
+            flows = api.Flows(tree, Dd, Dd, pa, pb)
+            cost = api.flowtree_batch(tree, tree.points, Dd, Dd, flows.pair_a, flows.pair_b, flows=flows)
+            plain = api.flowtree_batch(tree, tree.points, Dd, Dd, flows.pair_a, flows.pair_b)
+            assert tree.status() == 0
+            assert torch.equal(cost, plain)
+            # the saved distances through the adjoint
+            g = api.flowtree_backward(tree, Dd, Dd, flows, tree.points, torch.ones(n, device="cuda"))
+            res.append((cost.cpu().numpy(), flows.export(), g.cpu().numpy()))
+    for cost, ex, g in res[1:]:
+        assert np.array_equal(cost, res[0][0])
+        assert np.array_equal(g, res[0][2])
+        for i in range(n):
+            assert all(np.array_equal(x, y) for x, y in zip(ex[i], res[0][1][i])), i
+    Sd = oracle_supports(otree, db)
+    sel = np.arange(0, n, 15)
+    ref = _oracle_costs(otree, pts, Sd, Sd, pa[sel], pb[sel])
+    np.testing.assert_allclose(res[-1][0][sel].astype(np.float64), ref, rtol=REL, atol=1e-30)
