@@ -35,6 +35,7 @@ import time
 
 import numpy as np
 
+T_START = time.time()
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -503,12 +504,19 @@ def main():
                      "kernel": flow_kernel(tree, Q, D), "kernel_ms": kms,
                      "peak_basis": "%d SMs x %d lanes x %.0f MHz (%s sm_max_mhz)" % (n_sm, ALU_LANES_PER_SM, sm_clock, pk_kind)},
     }
+    if rank == 0:
+        progress("main leg: %.4g pairs/s" % value)
     if rank == 0 and world == 1 and not args.no_extras:
         line.update(extras(args, tree, D, Q, q_h, db_h, pts, shift, value, dev, pk, pk_kind))
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def progress(msg):
+    """One line per finished leg on stderr (the JSON line alone goes to stdout)."""
+    print("[bench %7.1f s] %s" % (time.time() - T_START, msg), file=sys.stderr, flush=True)
 
 
 def extras(args, tree, D, Q, q_h, db_h, pts, shift, batched_value, dev, pk, pk_kind):
@@ -523,6 +531,7 @@ def extras(args, tree, D, Q, q_h, db_h, pts, shift, batched_value, dev, pk, pk_k
     out["cpu_baseline"] = {"value": r_n, "unit": UNIT, "cores": cores, "kind": "oracle",
                            "sample": "%d random (query, db) pairs of the image workload, %.1f s" % (n_n, dt_n),
                            "single_thread": {"value": r_1, "sample_pairs": n_1}, "host": host_cpu()}
+    progress("cpu baseline")
     recall_job = None
     scale_data = None
     if not args.skip_scale:
@@ -533,6 +542,7 @@ def extras(args, tree, D, Q, q_h, db_h, pts, shift, batched_value, dev, pk, pk_k
             recall_job.start()
         except Exception as ex:  # report, do not lose the main line
             out["scale_knn_pipeline"] = {"error": "%s: %s" % (type(ex).__name__, ex)}
+    progress("scale data made, oracle recall started")
     # plain one-launch-per-pair form on a sample of the same pairs
     n_plain = 2000
     rng = np.random.default_rng(5)
@@ -550,6 +560,7 @@ def extras(args, tree, D, Q, q_h, db_h, pts, shift, batched_value, dev, pk, pk_k
                              "batched_speedup": batched_value / plain}
     out["match_depth_histogram"] = depth_histogram(tree, Q, D, pa, pb)
 
+    progress("plain form, depth histogram")
     # forward + backward (differentiation workload)
     nw, npairs = (30000, 4096) if not args.quick else (5000, 512)
     wl = synth.diff_pairs(n_words=nw, n_pairs=npairs)
@@ -616,6 +627,7 @@ def extras(args, tree, D, Q, q_h, db_h, pts, shift, batched_value, dev, pk, pk_k
                                           "note": "Flows.with_capacity rebound every step (pairs may change)"},
                       "workload": "vocab %d x 300 (1,000-cluster mixture), %d doc pairs, lengths 20-300" % (nw, npairs)}
 
+    progress("fwd+bwd")
     # text-shaped kNN pipeline
     nwt, ndb, nqt, k1 = (100000, 100000, 1000, 1000) if not args.quick else (20000, 10000, 100, 256)
     V = synth.mixture_vocab(nwt, 300, 1000, 0.3, 300)
@@ -655,6 +667,7 @@ def extras(args, tree, D, Q, q_h, db_h, pts, shift, batched_value, dev, pk, pk_k
         "workload": "vocab %d x 300, %d docs (log-normal lengths, Zipf(1.1) words), %d queries, top-%d -> top-%d"
                     % (nwt, ndb, nqt, k1, TOPK)}
 
+    progress("text pipeline")
     # the Mean method (centroid distance) as the first stage instead of the quadtree
     try:
         mws = torch.empty(api._ffi.load().ft_mean_scan_workspace_size(Q3.handle, D3.handle, k1), dtype=torch.uint8,
@@ -686,6 +699,7 @@ def extras(args, tree, D, Q, q_h, db_h, pts, shift, batched_value, dev, pk, pk_k
     except Exception as ex:  # report, do not lose the main line
         out["text_mean_prefilter"] = {"error": "%s: %s" % (type(ex).__name__, ex)}
 
+    progress("mean prefilter")
     # three-stage pipeline: quadtree -> top-1,000 -> Flowtree -> top-20 -> exact W1 -> top-10
     try:
         nq_x = 100 if not args.quick else 20
@@ -711,6 +725,7 @@ def extras(args, tree, D, Q, q_h, db_h, pts, shift, batched_value, dev, pk, pk_k
     except Exception as ex:  # report, do not lose the main line
         out["text_knn_exact_pipeline"] = {"error": "%s: %s" % (type(ex).__name__, ex)}
 
+    progress("three-stage pipeline")
     if scale_data is not None:
         try:
             out["scale_knn_pipeline"], got, lib = scale_leg(args, dev, pk, pk_kind, scale_data)
@@ -718,6 +733,7 @@ def extras(args, tree, D, Q, q_h, db_h, pts, shift, batched_value, dev, pk, pk_k
         except Exception as ex:  # report, do not lose the main line
             out["scale_knn_pipeline"] = {"error": "%s: %s" % (type(ex).__name__, ex)}
 
+    progress("scale pipeline")
     # random-model planted experiment (Sec. 4.2 model, Sec. 5.1 figure "Results on random data")
     try:
         from paper_1910_04126_gb300 import planted
@@ -739,6 +755,7 @@ def extras(args, tree, D, Q, q_h, db_h, pts, shift, batched_value, dev, pk, pk_k
     except Exception as ex:  # report, do not lose the main line
         out["planted_random_model"] = {"error": "%s: %s" % (type(ex).__name__, ex)}
 
+    progress("planted experiment")
     if recall_job is not None:  # the oracle's exhaustive Flowtree of the scale leg, run beside the legs above
         recall_job.join()
         sc = out.get("scale_knn_pipeline", {})
@@ -756,6 +773,7 @@ def extras(args, tree, D, Q, q_h, db_h, pts, shift, batched_value, dev, pk, pk_k
             sc["oracle_recall_threads"] = recall_job.result["threads"]
         elif isinstance(sc, dict):
             sc["oracle_recall_error"] = recall_job.result.get("error", "not run")
+    progress("oracle recall joined")
     out["roofline_hbm"] = hbm_roofline(q_h, db_h, batched_value, pk, pk_kind)
     return out
 
@@ -848,6 +866,12 @@ class OracleRecall(threading.Thread):
 
     def run(self):
         try:
+            # lowest CPU priority for this thread and the oracle's worker threads (which inherit it on Linux),
+            # so that the GPU legs' host work and its BLAS threads are not starved meanwhile
+            try:
+                os.setpriority(os.PRIO_PROCESS, 0, 19)
+            except (AttributeError, OSError):
+                pass
             import oracle as O
             t0 = time.time()
             threads = max(1, (os.cpu_count() or 2) - 1)

@@ -356,8 +356,15 @@ def random_subset_docs(support: np.ndarray, n_points: int, n_docs: int, seed: in
     planted = np.sort(support)
     out = np.empty((n_docs, s), dtype=np.int64)
     todo = np.arange(n_docs)
-    while len(todo):  # draw whole rows, redraw the ones with a repeated point or equal to the planted support
-        d = rng.integers(0, n_points, (len(todo), s))
+    while len(todo):  # redraw the rows equal to the planted support
+        if n_points <= 4096:
+            # small ground sets: the first s of a random permutation per row (a row of s independent draws
+            # would repeat a point too often: for s = 100 of 200 points, all but about 1e-11 of the rows)
+            d = np.argsort(rng.random((len(todo), n_points)), axis=1)[:, :s]
+        else:
+            # large ground sets: s independent draws, rows with a repeated point redrawn (at s <= 100 and
+            # more than 4,096 points, at least 30% of the rows have none)
+            d = rng.integers(0, n_points, (len(todo), s))
         srt = np.sort(d, axis=1)
         bad = (np.diff(srt, axis=1) == 0).any(axis=1) | (srt == planted).all(axis=1)
         out[todo[~bad]] = d[~bad]

@@ -1,5 +1,6 @@
 """Inputs of the random-model experiment (Sec. 4.2): the spherical-cap sampler
 and the single-swap candidate set."""
+import pytest
 import numpy as np
 from scipy import integrate, stats
 
@@ -57,3 +58,24 @@ def test_random_subset_competitors():
         w = d.word[d.row_ptr[i]:d.row_ptr[i + 1]]
         assert len(w) == 4 and len(set(w.tolist())) == 4 and w.min() >= 0 and w.max() < 50
         assert not np.array_equal(np.sort(w), planted)
+
+
+@pytest.mark.parametrize("n_points,s", [(200, 100), (20, 10), (5000, 100)])
+def test_random_subset_competitors_dense_supports(n_points, s):
+    """Supports of half the ground set (s = 100 of N = 200, the model's smallest N at s = 100): every row holds s
+    distinct points of the ground set and differs from the planted support; the draw finishes (s independent
+    draws per row would almost never be distinct here)."""
+    support = np.arange(s) * (n_points // s)
+    d = synth.random_subset_docs(support, n_points, 2000, seed=3)
+    assert d.n == 2001
+    rows = d.word.reshape(d.n, s)
+    assert np.array_equal(rows[0], support)
+    planted = np.sort(support)
+    srt = np.sort(rows[1:], axis=1)
+    assert np.all(np.diff(srt, axis=1) > 0) and srt.min() >= 0 and srt.max() < n_points
+    assert not np.any(np.all(srt == planted, axis=1))
+    # every point of the ground set is drawn about equally often (uniform s-subsets)
+    counts = np.bincount(rows[1:].reshape(-1), minlength=n_points)
+    expect = 2000 * s / n_points
+    tol = 6.0 * np.sqrt(expect)  # six standard deviations of a count
+    assert counts.min() > expect - tol and counts.max() < expect + tol
