@@ -31,7 +31,7 @@ constexpr int CHUNK = 64;       // sorted contributions per warp
 constexpr int COLS = 3;         // row vectors per lane in one column block (block = 96 vectors)
 constexpr int CHAIN_WARPS = 8;  // warps per CTA of a long chain
 constexpr int SHORT_CHAIN = 16; // longest chain one warp sums alone
-constexpr int BATCH = 4;        // contributions whose rows are loaded together
+constexpr int BATCH = 2;        // contributions whose rows are loaded together
 
 __device__ __forceinline__ void vzero(float& a) { a = 0.0f; }
 __device__ __forceinline__ void vzero(float4& a) { a = make_float4(0.0f, 0.0f, 0.0f, 0.0f); }
@@ -165,8 +165,10 @@ __device__ __forceinline__ void flush_run(V (&acc)[COLS], uint32_t cur, int64_t 
 // per run.  Lane q of a 32-entry window holds contribution q (point, other
 // point, coefficient); the warp walks the window in order, BATCH
 // contributions at a time with their row loads in flight together.
+// Three resident CTAs per SM (at most 80 registers per thread): more warps
+// waiting on the row gathers beat more rows in flight per warp.
 template <int VEC>
-__global__ void __launch_bounds__(256) k_bwd_runs(const uint32_t* __restrict__ key, const uint32_t* __restrict__ perm,
+__global__ void __launch_bounds__(256, 3) k_bwd_runs(const uint32_t* __restrict__ key, const uint32_t* __restrict__ perm,
                                                   int64_t n, uint32_t sentinel, const uint32_t* __restrict__ s_wa,
                                                   const uint32_t* __restrict__ s_wb, const float* __restrict__ s_coef,
                                                   const float* __restrict__ vocab, int dim, float* __restrict__ grad,
