@@ -178,6 +178,7 @@ def profile_backward(args):
     n = args.profile_backward
     wl = synth.diff_pairs(n_words=30000, n_pairs=n)
     tree = api.Tree(torch.as_tensor(wl.points, device="cuda"), wl.levels, wl.shift)
+    tree.set_config(*[int(x) for x in args.config.split(",")])
     A, B = api.Docs.from_csr(tree, wl.db), api.Docs.from_csr(tree, wl.queries)
     idx = torch.arange(n, dtype=torch.int32, device="cuda")
     flows = api.Flows(tree, A, B, idx, idx)
@@ -187,7 +188,7 @@ def profile_backward(args):
         api.flowtree_batch(tree, tree.points, A, B, flows.pair_a, flows.pair_b, flows=flows)
         api.flowtree_backward(tree, A, B, flows, tree.points, gcost, grad_vocab=gv)
     torch.cuda.synchronize()
-    print("profile backward done: %d pairs, status %d" % (n, tree.status()))
+    print("profile backward done: %d pairs, config %s, status %d" % (n, args.config, tree.status()))
 
 
 # ---------------------------------------------------------------------------
