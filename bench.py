@@ -80,7 +80,7 @@ def parse():
     ap.add_argument("--quick", action="store_true", help="small workload (smoke of the bench itself)")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--skip-scale", action="store_true", help="omit the 1,000,000-document scale leg")
-    ap.add_argument("--recall-oracle-queries", type=int, default=4,
+    ap.add_argument("--recall-oracle-queries", type=int, default=10,
                     help="scale leg: queries whose exhaustive top-10 the CPU oracle computes (on all host cores but "
                          "one, beside the GPU legs; about 40 s each on 16 Grace cores)")
     ap.add_argument("--profile-case", nargs=2, type=int, metavar=("N_DB", "N_Q"),

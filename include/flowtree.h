@@ -184,10 +184,9 @@ ft_status ft_flowtree_batch(const ft_tree* t, const float* vocab_dev, const ft_d
 /* Allocation-free variant of ft_flowtree_batch (the paper has no
  * counterpart; this is a deployment convenience).  For callers that cannot
  * allocate device memory at all -- a host whose device memory is held by its
- * own pooled allocator with nothing exposed to plug-ins, a latency-bound
- * loop where cudaMalloc's implicit device synchronisation is not allowed, or
- * code that would have to allocate while a stream is being captured -- and
- * so cannot provide ft_flowtree_batch's workspace.  Same inputs and outputs
+ * own pooled allocator with nothing exposed to plug-ins, or a latency-bound
+ * loop where cudaMalloc's implicit device synchronisation is not allowed --
+ * and so cannot provide ft_flowtree_batch's workspace.  Same inputs and outputs
  * (no saved flows); the workspace comes from a fixed device array of
  * FT_STATIC_SCRATCH_BYTES compiled into the library, held by every GPU that
  * loads it until the library is unloaded.  Calls no cudaMalloc/cudaFree.
@@ -201,7 +200,7 @@ ft_status ft_flowtree_batch(const ft_tree* t, const float* vocab_dev, const ft_d
  *     errors (FT_EUNSUPPORTED for a configuration the device cannot run) are
  *     returned as ft_flowtree_batch would return them.
  *   - The first call on a device (with that device current) looks up the
- *     array's device address; make that first call before any stream capture.
+ *     array's device address (cudaGetSymbolAddress) on that call only.
  *     The address is cached per device ordinal for the life of the process:
  *     it does not survive cudaDeviceReset (or any other teardown of the
  *     device's primary context), after which this entry point must not be

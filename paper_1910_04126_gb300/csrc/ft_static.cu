@@ -5,17 +5,16 @@
 // workspace (work-queue counter, longest-first pair order and its sort
 // buffers, and shared-memory overflow space for unusually long pairs).  Some
 // callers have no way to provide one: a host whose device memory is owned by
-// its own pooled allocator that exposes no allocation to plug-ins, code that
-// must not call cudaMalloc because it would implicitly synchronise the device
-// inside a latency-bound loop, or code that would otherwise have to allocate
-// while a stream is being captured into a CUDA graph.  This entry point takes
+// its own pooled allocator that exposes no allocation to plug-ins, or code
+// that must not call cudaMalloc because it would implicitly synchronise the
+// device inside a latency-bound loop.  This entry point takes
 // the same inputs and outputs but carves the workspace out of a fixed device
 // array compiled into the library.
 //
 // The array (FT_STATIC_SCRATCH_BYTES) lives in every GPU that loads the
 // library, for as long as the library stays loaded.  Its device address is
 // looked up once per device, on the first call made with that device
-// current; make that first call before any stream capture.  All calls share
+// current (cudaGetSymbolAddress, on that call only).  All calls share
 // the array: two calls whose work overlaps on the GPU (different streams, or
 // different host threads, without ordering between them) race on it and give
 // undefined results.  Serialise them on one stream.
