@@ -733,6 +733,11 @@ extern "C" ft_status ft_flowtree_autotune(ft_tree* t, const float* vocab_dev, co
         if (t->dim > 8)  // the deep-loads build (8-lane-group pricing)
             for (int w : {2, 4, 7}) cands.push_back({w, cap, FT_ALGO_WARP, 0, 1});
     }
+    // smaller stagings: more resident warps and a larger L1, longer pairs from the workspace
+    for (int cap : {128, 160, 192, 224}) {
+        if (cap >= maxn) continue;
+        for (int w : {2, 4, 6}) cands.push_back({w, cap, FT_ALGO_WARP, 0, 0});
+    }
     // the blocked form: warps per CTA x the warp's staging (0 = default; longer pairs take a CTA each)
     for (int w : {2, 3, 4, 6, 8}) {
         for (int st : {0, 1}) cands.push_back({w, 0, FT_ALGO_BLOCKED, st, 0});
