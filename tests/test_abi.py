@@ -84,3 +84,25 @@ def test_status_strings_name_every_code():
     for code, name in _ffi.STATUS.items():
         assert lib.ft_status_string(code).decode().split(":")[0] == name
     assert lib.ft_status_string(-99).decode() == "unknown ft_status"
+
+
+def _header_struct_fields(name):
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    m = re.search(r"typedef struct\s*\{([^}]*)\}\s*" + name + r"\s*;", text)
+    assert m, name
+    return re.findall(r"\b(u?int\d+_t|float|double)\s+([a-z_0-9]+)\s*;", m.group(1))
+
+
+def test_binding_structs_match_the_header():
+    """The ctypes mirrors of the header's by-value structs have the same fields, in order, with the same widths."""
+    import ctypes as C
+    from paper_1910_04126_gb300 import _ffi
+    width = {"int32_t": C.c_int32, "int64_t": C.c_int64, "uint32_t": C.c_uint32, "uint64_t": C.c_uint64,
+             "float": C.c_float, "double": C.c_double}
+    for cname, py in (("ft_flowtree_config", _ffi.FlowtreeConfig), ("ft_tree_info", _ffi.TreeInfo),
+                      ("ft_docs_info", _ffi.DocsInfo)):
+        fields = _header_struct_fields(cname)
+        assert [n for _, n in fields] == [n for n, _ in py._fields_], cname
+        assert all(width[t] is ct for (t, _), (_, ct) in zip(fields, py._fields_)), cname
+    assert "deep_loads" in [n for n, _ in _ffi.FlowtreeConfig._fields_]
