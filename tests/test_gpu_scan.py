@@ -151,3 +151,30 @@ def test_scan_matches_count():
     m = api.quadtree_scan_matches(tree, Dq, D)
     assert m == api.quadtree_scan_matches(tree, Dq, D1) + api.quadtree_scan_matches(tree, Dq, D2)
     assert m > 0
+
+
+@pytest.mark.parametrize("n,k,kind", [(1, 1, "rand"), (100, 37, "ties3"), (4095, 4095, "ties3"), (4096, 4096, "rand"),
+                                      (4097, 4096, "ties3"), (100000, 4096, "equal"), (300003, 1000, "ties3"),
+                                      (300003, 4096, "rand"), (200000, 10, "inf")])
+def test_topk_f32_select_edge_cases(n, k, kind):
+    """The radix select (11-bit digits, early exit once the prefix's keys fit its 4,096-entry buffer) against a
+    plain stable sort: ascending values, ties to the smaller column; ragged row lengths around the buffer size,
+    k at the buffer size, all-equal rows (the digits run out on the values and decide on the columns), three
+    distinct values, and +inf entries."""
+    rng = np.random.default_rng(n + k)
+    rows = 3
+    if kind == "rand":
+        v = rng.random((rows, n)).astype(np.float32)
+    elif kind == "ties3":
+        v = rng.integers(0, 3, (rows, n)).astype(np.float32)
+    elif kind == "equal":
+        v = np.full((rows, n), 0.5, np.float32)
+    else:
+        v = rng.random((rows, n)).astype(np.float32)
+        v[:, rng.integers(0, n, n // 2)] = np.inf
+    ids, vals = api.topk_f32(torch.as_tensor(v, device="cuda"), k)
+    ids, vals = ids.cpu().numpy(), vals.cpu().numpy()
+    for r in range(rows):
+        want = np.lexsort((np.arange(n), v[r]))[:k]  # by value, then by column
+        assert np.array_equal(ids[r], want), r
+        assert np.array_equal(vals[r], v[r][want])
