@@ -85,9 +85,9 @@ __global__ void __launch_bounds__(256) k_flowtree_blocked(FlowCtx c, int grab, i
     const int warp = int(threadIdx.x >> 5);
     const unsigned lane = lane_id();
     const Tables tb = tables_bytes > 0 ? stage_tables(c, smem) : Tables{c.vocab, c.rmq};
-    const BlockedBuf w =
-        carve_blockedbuf(smem + tables_bytes + size_t(warp) * blockedbuf_bytes(cap, PT16, blocked_has_meta(PT16, SAVE)),
-                         cap, PT16, blocked_has_meta(PT16, SAVE));
+    constexpr bool META = blocked_has_meta(PT16, SAVE), QUEUE = blocked_has_queue(MODE);
+    const BlockedBuf w = carve_blockedbuf(smem + tables_bytes + size_t(warp) * blockedbuf_bytes(cap, PT16, META, QUEUE),
+                                          cap, PT16, META, QUEUE);
     const int64_t n_pairs = c.n_pairs;
     for (;;) {
         unsigned long long first = 0;
@@ -427,7 +427,8 @@ ft_status make_plan_algo(const ft_tree* t, const ft_docs* a, const ft_docs* b, i
         capw = std::min(std::min(capw, need), kBlockedCap);
         p->cap = capw;
         p->smem = size_t(p->tables_bytes) +
-                  size_t(p->warps) * blockedbuf_bytes(p->cap, blocked_pt16(t), blocked_has_meta(blocked_pt16(t), save));
+                  size_t(p->warps) * blockedbuf_bytes(p->cap, blocked_pt16(t), blocked_has_meta(blocked_pt16(t), save),
+                                                      blocked_has_queue(mode));
         if (p->smem > size_t(max_smem)) return FT_EUNSUPPORTED;
         int bps = 0;
         p->kernel = blocked_kernel(t, mode, save);

@@ -43,8 +43,8 @@ struct BlockedBuf {
     uint32_t* it;     // [cap] items (it_make)
     uint32_t* list;   // [cap] items that match at the current depth: position | run head << 16
     uint32_t* M;      // [cap] at run heads: the run's matched mass min(mu total, nu total)
-    uint32_t* qe;     // [64] queued pairs: (PT16) mu point | nu point << 16, else mu index | nu index << 16
-    uint32_t* qf;     // [64] their flow
+    uint32_t* qe;     // (queue) [64] queued pairs: (PT16) mu point | nu point << 16, else mu index | nu index << 16
+    uint32_t* qf;     // (queue) [64] their flow
     uint32_t* wd;     // (not PT16) [cap] ground-point ids of the two supports (mu items, then nu items)
     uint16_t* meta;   // (with meta) [cap] bit 15 side (0 mu, 1 nu), bits 0..14 index in its support
     uint16_t* pt;     // (PT16) [cap] ground-point id of the item at each position
@@ -53,21 +53,26 @@ struct BlockedBuf {
 // PT16: ground sets of at most 65,536 points (16-bit point ids per position).
 // The support indices (meta) are kept when flows are saved or the pricing
 // resolves point ids through them (not PT16).
-__host__ __device__ inline bool blocked_has_meta(bool pt16, bool save) { return save || !pt16; }
+__host__ __device__ constexpr bool blocked_has_meta(bool pt16, bool save) { return save || !pt16; }
 
-__host__ __device__ inline size_t blockedbuf_bytes(int cap, bool pt16, bool meta) {
-    return (size_t(cap + 1) * 8 + size_t(cap) * (12 + (meta ? 2 : 0) + (pt16 ? 2 : 4)) + 512 + 15) & ~size_t(15);
+// The pricing queue (qe, qf) exists for the 8-lane-group pricing only (dim
+// > 8); with small dims every lane prices its own pairs as they are found.
+__host__ __device__ constexpr bool blocked_has_queue(int mode) { return mode != 0; }
+
+__host__ __device__ inline size_t blockedbuf_bytes(int cap, bool pt16, bool meta, bool queue) {
+    return (size_t(cap + 1) * 8 + size_t(cap) * (12 + (meta ? 2 : 0) + (pt16 ? 2 : 4)) + (queue ? 512 : 0) + 15) &
+           ~size_t(15);
 }
 
-__device__ __forceinline__ BlockedBuf carve_blockedbuf(uint8_t* base, int cap, bool pt16, bool meta) {
+__device__ __forceinline__ BlockedBuf carve_blockedbuf(uint8_t* base, int cap, bool pt16, bool meta, bool queue) {
     BlockedBuf w;
     w.G = reinterpret_cast<uint64_t*>(base);
     w.it = reinterpret_cast<uint32_t*>(w.G + cap + 1);
     w.list = w.it + cap;
     w.M = w.list + cap;
-    w.qe = w.M + cap;
-    w.qf = w.qe + 64;
-    w.wd = w.qf + 64;
+    w.qe = queue ? w.M + cap : nullptr;
+    w.qf = queue ? w.qe + 64 : nullptr;
+    w.wd = queue ? w.qf + 64 : w.M + cap;
     w.meta = reinterpret_cast<uint16_t*>(w.wd + (pt16 ? 0 : cap));
     w.pt = w.meta + (meta ? cap : 0);
     return w;
@@ -554,7 +559,16 @@ __device__ float flowtree_pair_blocked(const FlowCtx& c, const BlockedBuf& w, co
             const unsigned emask = __ballot_sync(FULL_MASK, emit);
             if (emask == 0) continue;
             const int qp = __popc(emask & lmask_lt);
-            if (emit) {
+            if (MODE == 0) {
+                // small dim: each emitting lane prices its own pair at once (no queue)
+                if (emit) {
+                    const uint32_t wa = PT16 ? qa : w.wd[ia];
+                    const uint32_t wb = PT16 ? qb : w.wd[na + ib];
+                    const float dist = dist_lane(tb, c.dim, wa, wb);
+                    acc.add(float(f) * dist);
+                    if (SAVE) c.f_dist[slot0 + n_saved + qp] = dist;
+                }
+            } else if (emit) {
                 w.qe[qn + qp] = PT16 ? (qa | (qb << 16)) : (ia | (ib << 16));
                 w.qf[qn + qp] = f;
             }
@@ -568,7 +582,7 @@ __device__ float flowtree_pair_blocked(const FlowCtx& c, const BlockedBuf& w, co
                 }
                 n_saved += __popc(emask);
             }
-            qn += __popc(emask);
+            if (MODE != 0) qn += __popc(emask);
             if (qn >= 32) {
                 __syncwarp();
                 price_staged<MODE, SAVE, PT16>(c, w, tb, na, 32, qslot, acc);
